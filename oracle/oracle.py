@@ -1,0 +1,181 @@
+"""CPU oracle for the fully discrete Lax--Oleinik scheme (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+may import this module.  It wraps ``hjlo_oracle.c`` (plain C, binary64,
+``-ffp-contract=off``) with ctypes and adds the few readouts the paper defines
+on top of the scheme.  It shares no code with the CUDA library.
+
+Paper: Bouillard, Faou & Zavidovique, "Fast weak-KAM integrators for separable
+Hamiltonian systems".  Sec. 2.3 eq. cost2/eqconvol (one step), Remark rk28
+(axis splitting), eq. uN (time loop), Sec. 3.3 eq. los (torus grid, lift-
+minimised cost), Prop. prop:klm (discrete effective Hamiltonian), Appendix B
+eq. raslebol (discrete optimal path; the adjoint follows it).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hjlo_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libhjlo_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (binary64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            P = ctypes.POINTER
+            L.hjo_kernel.restype = f64
+            L.hjo_kernel.argtypes = [i64, f64, f64, f64]
+            L.hjo_window.restype = i32
+            L.hjo_window.argtypes = [i64, f64, f64, f64, i64, P(i64), P(i64)]
+            L.hjo_table.restype = None
+            L.hjo_table.argtypes = [i64, i64, f64, f64, f64, P(f64)]
+            run_args = [i32, P(i64), P(f64), f64, P(f64), P(i64), ctypes.c_void_p,
+                        ctypes.c_void_p, i64, i64, ctypes.c_void_p, i32]
+            L.hjo_run_f64.restype = i32
+            L.hjo_run_f64.argtypes = run_args
+            L.hjo_run_f32.restype = i32
+            L.hjo_run_f32.argtypes = run_args
+            L.hjo_adjoint_f64.restype = i32
+            L.hjo_adjoint_f64.argtypes = [i32, P(i64), P(f64), f64, P(f64), P(i64), P(f64),
+                                          ctypes.c_void_p, i64, i64, P(f64), P(f64), P(f64),
+                                          P(f64), i32]
+            L.hjo_max_threads.restype = i32
+            L.hjo_max_threads.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _vec(x, n, dtype):
+    a = np.atleast_1d(np.asarray(x, dtype=dtype))
+    if a.size == 1 and n > 1:
+        a = np.repeat(a, n)
+    if a.size != n:
+        raise ValueError("expected %d per-axis values, got %d" % (n, a.size))
+    return np.ascontiguousarray(a)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def max_threads() -> int:
+    return int(lib().hjo_max_threads())
+
+
+def kernel(d: int, dx: float, h: float, P: float) -> float:
+    """k[d] = h*L(d*dx/h), L(v) = v^2/2 - P v (eq. cost2, pinned binary64 order)."""
+    return float(lib().hjo_kernel(int(d), float(dx), float(h), float(P)))
+
+
+def window(N: int, dx: float, h: float, P: float, W: int) -> tuple[int, int]:
+    """Displacement window [dlo, dhi]: 2W+1 centred on the kernel minimiser, or
+    the N lift-minimising displacements when W <= 0 or 2W+1 >= N (eq. los)."""
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    if lib().hjo_window(int(N), float(dx), float(h), float(P), int(W), ctypes.byref(lo), ctypes.byref(hi)):
+        raise ValueError("invalid window arguments")
+    return lo.value, hi.value
+
+
+def table(N: int, dx: float, h: float, P: float, W: int):
+    """(dlo, dhi, k) with k[d - dlo] for d in [dlo, dhi]."""
+    dlo, dhi = window(N, dx, h, P, W)
+    k = np.empty(dhi - dlo + 1, dtype=np.float64)
+    lib().hjo_table(dlo, dhi, float(dx), float(h), float(P), _ptr(k, ctypes.c_double))
+    return dlo, dhi, k
+
+
+def run(u0, dx, h, P, W, V=None, nsteps: int = 1, *, V_per_step: bool = False,
+        record_argmin: bool = False, nthreads: int = 0):
+    """nsteps of the scheme (eq. uN), returning u^nsteps (and argmins).
+
+    u0: binary64 or binary32 array (1..3 dims, last axis contiguous); a
+    binary32 array selects the binary32-storage scheme.  V: None, an array of
+    u0's shape (time-independent) or, with V_per_step, shape (nsteps, *shape).
+    Argmins are the displacement d of every pass, shape (nsteps, ndim, *shape).
+    """
+    u0 = np.asarray(u0)
+    if u0.dtype not in (np.float64, np.float32):
+        raise TypeError("u0 must be float64 or float32")
+    ndim = u0.ndim
+    shape = _vec(u0.shape, ndim, np.int64)
+    dxv, Pv, Wv = _vec(dx, ndim, np.float64), _vec(P, ndim, np.float64), _vec(W, ndim, np.int64)
+    u = np.array(u0, copy=True, order="C")
+    npts = u.size
+    vptr, vstride = None, 0
+    if V is not None:
+        Va = np.ascontiguousarray(V, dtype=np.float64)
+        want = (nsteps, *u.shape) if V_per_step else u.shape
+        if Va.shape != tuple(want):
+            raise ValueError("V has shape %s, expected %s" % (Va.shape, want))
+        vptr, vstride = Va.ctypes.data, (npts if V_per_step else 0)
+    amin = None
+    if record_argmin:
+        amin = np.zeros((nsteps, ndim, *u.shape), dtype=np.int32)
+    fn = lib().hjo_run_f64 if u.dtype == np.float64 else lib().hjo_run_f32
+    rc = fn(ndim, _ptr(shape, ctypes.c_int64), _ptr(dxv, ctypes.c_double), float(h),
+            _ptr(Pv, ctypes.c_double), _ptr(Wv, ctypes.c_int64), u.ctypes.data, vptr, vstride,
+            int(nsteps), None if amin is None else amin.ctypes.data, int(nthreads))
+    if rc:
+        raise ValueError("oracle rejected its arguments")
+    return (u, amin) if record_argmin else u
+
+
+def adjoint(u0, dx, h, P, W, V, nsteps: int, ubar_n, *, V_per_step: bool = False, nthreads: int = 0):
+    """Gradient of J = <ubar_n, u^nsteps> w.r.t. u^0, P (per axis) and V.
+
+    Follows the discrete optimal path (eq. raslebol): each value of a pass came
+    from exactly one source, so the cotangent is routed back along the argmin.
+    Returns (ubar0, Pbar, Vbar); Vbar has V's shape (static or per step).
+    """
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    ndim = u0.ndim
+    shape = _vec(u0.shape, ndim, np.int64)
+    dxv, Pv, Wv = _vec(dx, ndim, np.float64), _vec(P, ndim, np.float64), _vec(W, ndim, np.int64)
+    npts = u0.size
+    if V is None:
+        V = np.zeros(u0.shape)
+        V_per_step = False
+    Va = np.ascontiguousarray(V, dtype=np.float64)
+    ub = np.ascontiguousarray(ubar_n, dtype=np.float64)
+    ubar0 = np.zeros_like(u0)
+    Pbar = np.zeros(ndim)
+    Vbar = np.zeros(Va.shape)
+    rc = lib().hjo_adjoint_f64(ndim, _ptr(shape, ctypes.c_int64), _ptr(dxv, ctypes.c_double), float(h),
+                               _ptr(Pv, ctypes.c_double), _ptr(Wv, ctypes.c_int64),
+                               _ptr(u0, ctypes.c_double), Va.ctypes.data, npts if V_per_step else 0,
+                               int(nsteps), _ptr(ub, ctypes.c_double), _ptr(ubar0, ctypes.c_double),
+                               _ptr(Pbar, ctypes.c_double), _ptr(Vbar, ctypes.c_double), int(nthreads))
+    if rc:
+        raise ValueError("oracle rejected its arguments")
+    return ubar0, Pbar, Vbar
+
+
+def hbar_estimate(u0, un, nsteps: int, h: float):
+    """Discrete effective Hamiltonian readout (Prop. prop:klm, sign of u_t + H = 0):
+    (-mean, -max, -min) of (u^n - u^0)/(n h) over the grid."""
+    r = (np.asarray(un, dtype=np.float64) - np.asarray(u0, dtype=np.float64)) / (nsteps * h)
+    return float(-r.mean()), float(-r.max()), float(-r.min())
