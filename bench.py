@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Throughput of the fully discrete Lax--Oleinik scheme on GB300.
+
+One benchmark step = one complete run of a workload from its initial data
+(default: grid1024, the 2D 1024^2 torus, W = 64, 1000 time steps, binary64)
+through the library's C ABI.  The metric is grid-point updates per second
+(points x time steps / time); every result is bit-exact against the CPU
+oracle (tests/test_gpu_parity.py).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload grid1024|cube256|line256] [--algo monge|brute]
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the plan's stream; before each timed step the state is reset to u0 and a
+256 MiB buffer is written to flush L2 (the 8 MiB grid of grid1024 is then
+L2-resident within a step, as in any run of that size).  Barrier and device
+synchronisation on both sides of the timed region; the max over ranks is
+reported.  Under torchrun every rank runs an independent replica (the single
+grid does not shard: "replicas only"); value = all ranks' updates / max time.
+
+The JSON line also carries: e2e (the same run through hjlo_run_host from
+page-locked host buffers, copies inside the timed region), roofline of the
+dominant kernel (the axis pass), the CPU oracle timed on a bounded sample of
+the same workload (cpu_baseline), SM clocks sampled during the timed region
+and the number of kernels launched.  --impl reference times the CPU oracle
+alone (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1210_4090_gb300 import workloads as WL  # noqa: E402
+
+METRIC = "grid-point updates/s"
+UNIT = "updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256"], default="grid1024")
+    ap.add_argument("--algo", choices=["monge", "brute", "auto"], default="monge")
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    return WL.WORKLOADS[name]()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1210_4090_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(workload_name, algo, dtype):
+    """DRAM bytes per pass launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_%s_%s_%s.txt" % (workload_name, algo, dtype))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.split(":", 1)[0].strip() in ("kernel_source_hash", "dram_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(statistics.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_oracle_rate(p, budget_s):
+    """The oracle as it stands on the host cores, on the first time steps of the
+    same workload; returns (updates/s, cores, sample description)."""
+    from oracle import oracle as O
+    cores = O.max_threads()
+    t0 = time.perf_counter()
+    u = O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, 1)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(p.nsteps - 1, budget_s / max(t1, 1e-9))))
+    t0 = time.perf_counter()
+    O.run(u, p.dx, p.h, p.P, p.W, p.V, n)
+    dt = time.perf_counter() - t0
+    rate = p.npts * n / dt
+    sample = "%s %s, time steps 2..%d of %d (%d steps, %.1f s), %d OpenMP threads" % (
+        p.name, "x".join(map(str, p.shape)), n + 1, p.nsteps, n, dt, cores)
+    return rate, cores, sample
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    from oracle import oracle as O
+    O.build()
+    per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(p, per / 2)
+    rates, samples = [], []
+    for _ in range(args.steps):
+        r, cores, s = cpu_oracle_rate(p, per)
+        rates.append(r)
+        samples.append(s)
+    value = float(statistics.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": p.npts * p.nsteps / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": p.name, "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
+                       "h": p.h, "P": list(p.P), "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": samples[0]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1210_4090_gb300 import hjlo
+
+    p = workload(args.workload)
+    algo = {"monge": hjlo.ALGO_MONGE, "brute": hjlo.ALGO_BRUTE, "auto": hjlo.ALGO_AUTO}[args.algo]
+    code = hjlo.F64 if args.dtype == "f64" else hjlo.F32_STORAGE
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W, dtype=code, algo=algo)
+    info = plan.info()
+    dev = torch.device("cuda", local)
+    u0 = torch.tensor(p.u0, dtype=tdt, device=dev)
+    Vt = torch.tensor(p.V, dtype=torch.float64, device=dev)
+    u = torch.empty_like(u0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def one():
+        plan.run(u, Vt, p.nsteps)
+
+    for _ in range(max(3, args.warmup)):
+        u.copy_(u0)
+        one()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_uuid = None
+    clocks = ClockSampler(gpu_uuid)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for _ in range(args.steps):
+        u.copy_(u0)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    updates = p.npts * p.nsteps
+    value = world * updates * args.steps / (total_ms * 1e-3)
+    cnt = plan.sync()
+
+    # roofline of the dominant kernel: the axis pass (ndim launches per time
+    # step; the h*V kernel is one launch per run and is left in the average)
+    launches_per_step = p.ndim * p.nsteps
+    avg_launch_s = ms_per_step * 1e-3 / launches_per_step
+    esize = 8 if args.dtype == "f64" else 4
+    alg_bytes_step = p.npts * (p.ndim * 2 * esize + 8)          # per time step
+    alg_bytes_launch = alg_bytes_step / p.ndim
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    achieved = alg_bytes_launch / avg_launch_s / 1e9
+    traffic = profile_traffic(args.workload, info["algo"], args.dtype)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": "hjlo::pass_kernel (%s)" % info["algo"],
+            "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes_launch,
+            "avg_launch_us": avg_launch_s * 1e6,
+            "fp64_ops_per_launch": p.npts * 1.0 + (p.npts / p.ndim)}
+
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.empty(p.shape, dtype=tdt).pin_memory().numpy()
+        Vh = torch.empty(p.shape, dtype=torch.float64).pin_memory().numpy()
+        Vh[...] = p.V
+        ts = []
+        for k in range(args.steps + 1):
+            uh[...] = p.u0
+            t0 = time.perf_counter()
+            plan.run_host(uh, Vh, p.nsteps)
+            dt = time.perf_counter() - t0
+            if k:
+                ts.append(dt)
+        e2e = {"value": world * updates / float(np.mean(ts)), "unit": UNIT,
+               "h2d_bytes_per_step": int(p.npts * esize + p.npts * 8),
+               "d2h_bytes_per_step": int(p.npts * esize)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(p, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": p.name, "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
+                           "h": p.h, "P": list(p.P), "algo": info["algo"],
+                           "updates_per_step": updates,
+                           "l2": "256 MiB buffer written between timed steps; the grid is L2-resident "
+                                 "within a step when it fits",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(args.steps * (1 + launches_per_step)),
+                "counters": cnt}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * hjlo.h -- C ABI of the GB300 (sm_103a) solver for the fully discrete
+ * Lax--Oleinik scheme of Bouillard, Faou & Zavidovique, "Fast weak-KAM
+ * integrators for separable Hamiltonian systems".
+ *
+ * The scheme (Sec. 2.3, eq. eqconvol; Sec. 3.3, eq. los): on a periodic grid
+ * with space step dx_a along axis a and time step h (the paper's tau),
+ *
+ *     u^{n+1}(x) = min_y [ u^n(y) + sum_a k_a(x_a - y_a) ] - h V(t_n, x),
+ *     k_a[d]     = h * L_a(d dx_a / h),   L_a(v) = v^2/2 - P_a v
+ *
+ * (the mechanical Hamiltonian H = |p+P|^2/2 + V of eq. HPV; its Legendre
+ * dual of Sec. 2.1).  Because the kinetic part is separable the minimum is
+ * taken axis by axis (Remark rk28).  Conventions fixed by this library (the
+ * paper leaves them open):
+ *   - one step = a pass along axis 0 (slowest varying), then axis 1, ...,
+ *     then axis ndim-1 (contiguous), then the potential term;
+ *   - candidate = one binary64 round-to-nearest add fl(u[j] + k[d]); the
+ *     potential term is fl(m - fl(h V)); binary32 storage rounds each pass's
+ *     result to nearest binary32 (the last one after the potential term);
+ *   - window: displacements d in [c-W, c+W] where c is the largest minimiser
+ *     of k_a, or, when W <= 0 or 2W+1 >= N, the N displacements realising the
+ *     lift-minimised torus cost of eq. los (equal lift costs keep the larger d);
+ *   - argmin = the displacement d of the candidate kept; among equal values
+ *     the smallest lifted source j = i - d (the largest d) is kept.
+ * Results are identical, bit for bit, between the two algorithms below.
+ *
+ * Memory: every array argument is a device pointer unless its description
+ * says "host".  Arrays are C-contiguous (row-major, last axis contiguous) and
+ * owned by the caller; the library never frees them.  A plan owns its kernel
+ * tables, its copy of h*V, its status words and any captured CUDA graph.
+ * All work is enqueued on the plan's stream and returns without waiting,
+ * unless the description says it synchronises.
+ *
+ * Errors: every call returns an hjlo_status; none aborts, traps or exits.
+ * Argument errors are detected before any work is enqueued (HJLO_EINVAL,
+ * HJLO_EUNSUPPORTED).  CUDA errors map to HJLO_ECUDA.  hjlo_last_error()
+ * returns a description of the last failure on the calling thread.
+ */
+#ifndef HJLO_H
+#define HJLO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HJLO_VERSION 1
+#define HJLO_MAX_DIM 3
+
+typedef enum {
+    HJLO_OK = 0,
+    HJLO_EINVAL = 1,        /* invalid argument (bad sizes, NULL, non-positive steps) */
+    HJLO_ENOMEM = 2,        /* device allocation failed */
+    HJLO_ECUDA = 3,         /* a CUDA runtime or driver call failed */
+    HJLO_EPRECOND = 4,      /* a numerical precondition failed (see hjlo_counters) */
+    HJLO_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    HJLO_EUNSUPPORTED = 6   /* valid request this build cannot serve (e.g. line too long) */
+} hjlo_status;
+
+typedef enum {
+    HJLO_F64 = 0,           /* u stored and computed in binary64 */
+    HJLO_F32_STORAGE = 1    /* u stored in binary32, every candidate computed in binary64 */
+} hjlo_dtype;
+
+typedef enum {
+    HJLO_ALGO_AUTO = 0,     /* library's choice (results do not depend on it) */
+    HJLO_ALGO_BRUTE = 1,    /* every window candidate evaluated in binary64 */
+    HJLO_ALGO_MONGE = 2     /* monotone-argmin search (see hjlo_plan_create) */
+} hjlo_algo;
+
+/* Problem descriptor (one grid).  Sec. 2.3 eq. cost2 / eqconvol, Sec. 3.3. */
+typedef struct {
+    int32_t ndim;                 /* 1..3 */
+    int32_t dtype;                /* hjlo_dtype */
+    int32_t algo;                 /* hjlo_algo */
+    int32_t reserved;             /* must be 0 */
+    int64_t shape[HJLO_MAX_DIM];  /* N_a >= 1 per axis (entries >= ndim ignored) */
+    double dx[HJLO_MAX_DIM];      /* space step per axis, > 0 */
+    double h;                     /* time step (the paper's tau), > 0 */
+    double P[HJLO_MAX_DIM];       /* the vector P of eq. HPV */
+    int64_t window[HJLO_MAX_DIM]; /* W per axis; <= 0 or 2W+1 >= N: full torus window */
+} hjlo_desc;
+
+typedef struct hjlo_plan hjlo_plan;
+
+/* What a plan resolved (host struct filled by hjlo_plan_info). */
+typedef struct {
+    int32_t ndim;
+    int32_t algo;                 /* resolved algorithm: BRUTE or MONGE */
+    int64_t dlo[HJLO_MAX_DIM];    /* window [dlo, dhi] of displacements per axis */
+    int64_t dhi[HJLO_MAX_DIM];
+    int64_t centre[HJLO_MAX_DIM]; /* largest minimiser of k_a */
+    double kmin[HJLO_MAX_DIM];    /* min_d k_a[d] */
+    double curvature[HJLO_MAX_DIM]; /* min second difference of the k_a table */
+    int64_t npts;                 /* prod(shape) */
+} hjlo_plan_facts;
+
+/* Device-side counters of a plan (host struct filled by hjlo_sync). */
+typedef struct {
+    int64_t exact_rescans;        /* outputs whose binary32 screen left >1 survivor */
+    int64_t brute_fallback_lines; /* lines the monotone search handed to brute force */
+    int64_t steps;                /* time steps enqueued on this plan so far */
+    int32_t error_flags;          /* bit 0: precondition, bit 1: wait timeout */
+    int32_t reserved;
+} hjlo_counters;
+
+/*
+ * Create a plan for one grid on a CUDA stream (cudaStream_t, may be NULL for
+ * the default stream).  Builds the kernel tables k_a[d] of eq. cost2 on the
+ * host in the fixed binary64 order, resolves the window (eq. los, Sec. 4.2)
+ * and uploads them.  HJLO_ALGO_MONGE relies on the candidate matrix
+ * u[j] + k[i-j] being Monge, which holds because k_a is convex (hypothesis
+ * (i), Sec. 2.1): its row minima move monotonically, so each output is
+ * searched in a narrow range bracketed by its neighbours' argmins.  The plan
+ * checks that the table's second differences are positive; each launch
+ * re-checks the rounding margin per line and falls back to brute force for a
+ * line that fails it (counted in hjlo_counters).
+ * Errors: HJLO_EINVAL (bad descriptor), HJLO_EUNSUPPORTED (a line of the grid
+ * does not fit in one CTA's shared memory), HJLO_ENOMEM, HJLO_ECUDA.
+ */
+hjlo_status hjlo_plan_create(const hjlo_desc *desc, void *cuda_stream, hjlo_plan **out);
+
+/* Release a plan and everything it owns.  NULL is accepted.  Synchronises
+ * the plan's stream first. */
+hjlo_status hjlo_plan_destroy(hjlo_plan *plan);
+
+/* Copy the resolved windows and table facts into *info (host). */
+hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
+
+/*
+ * One time step (eq. eqconvol): u_out = T(u_in).  u_in and u_out hold npts
+ * values of the plan's dtype and may be the same pointer (in place).  V: npts
+ * binary64 values of V(t_n, .) or NULL for V = 0.  argmin_out: NULL, or
+ * ndim*npts int32 receiving the argmin displacement d of every pass, laid out
+ * [axis][point] (the discrete optimal path of eq. raslebol, one step).
+ */
+hjlo_status hjlo_step(hjlo_plan *plan, const void *u_in, void *u_out, const double *V,
+                      int32_t *argmin_out);
+
+/*
+ * nsteps time steps in place on u (eq. uN) with a time-independent V (NULL
+ * for V = 0).  h*V is formed once per call.  The step loop is replayed from a
+ * CUDA graph captured on first use for this (u, V) pair.
+ */
+hjlo_status hjlo_run(hjlo_plan *plan, void *u, const double *V, int64_t nsteps);
+
+/*
+ * Time-dependent potential: step n uses V + n*npts (V holds nsteps*npts
+ * binary64 values, V(t_n, .) for n = 0..nsteps-1).  In place on u.
+ */
+hjlo_status hjlo_run_tv(hjlo_plan *plan, void *u, const double *V, int64_t nsteps);
+
+/*
+ * End-to-end variant of hjlo_run for HOST buffers: copies u_host (and
+ * V_host, may be NULL) to plan-owned device memory, runs nsteps, copies the
+ * result back into u_host and synchronises.  u_host holds npts values of the
+ * plan's dtype (host), V_host npts binary64 (host).  Page-locked host memory
+ * gives the fastest copies.
+ */
+hjlo_status hjlo_run_host(hjlo_plan *plan, void *u_host, const double *V_host, int64_t nsteps);
+
+/*
+ * Discrete effective Hamiltonian readout (Prop. prop:klm with the sign of
+ * u_t + H = 0): r(x) = (u_n(x) - u_0(x)) / (nsteps h); writes to the HOST
+ * array out3 = { -mean_x r, -max_x r, -min_x r } (estimate, lower, upper).
+ * Synchronises the plan's stream.
+ */
+hjlo_status hjlo_hbar(hjlo_plan *plan, const void *u0, const void *un, int64_t nsteps,
+                      double *out3);
+
+/* Wait for the plan's stream and copy its device counters into *out (host,
+ * may be NULL).  Returns HJLO_EPRECOND / HJLO_ETIMEOUT if a launch since the
+ * last call raised the corresponding flag (the flags are then cleared). */
+hjlo_status hjlo_sync(hjlo_plan *plan, hjlo_counters *out);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *hjlo_last_error(void);
+
+/* HJLO_VERSION of the loaded library. */
+int32_t hjlo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJLO_H */

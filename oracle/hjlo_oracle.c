@@ -399,3 +399,57 @@ int hjo_adjoint_f64(int ndim, const int64_t *shape, const double *dx, double h, 
     hjo_geom_free(&g);
     return 0;
 }
+
+/* ------------------------------------------------------------- sampled step */
+
+/* Value after passes 0..a at the point y (coordinates), by the definition of
+ * the passes: min over the window of axis a of (value after passes 0..a-1 at
+ * y with y_a moved to the source) + k_a[d].  Pass -1 is u itself. */
+static double hjo_point_value(const hjo_geom *g, const double *u, int a, int64_t *y)
+{
+    if (a < 0) {
+        int64_t x = 0;
+        for (int b = 0; b < g->ndim; ++b) x = x * g->shape[b] + y[b];
+        return u[x];
+    }
+    int64_t N = g->shape[a], keep = y[a];
+    double best = 0.0;
+    int first = 1;
+    for (int64_t d = g->dhi[a]; d >= g->dlo[a]; --d) {
+        int64_t r = (keep - d) % N;
+        if (r < 0) r += N;
+        y[a] = r;
+        double cand = hjo_point_value(g, u, a - 1, y) + g->k[a][d - g->dlo[a]];
+        if (first || cand < best) { best = cand; first = 0; }
+    }
+    y[a] = keep;
+    return best;
+}
+
+/*
+ * One step of the binary64 scheme evaluated only at the listed points
+ * (flat row-major indices), for checking large grids by sampling.  V: NULL or
+ * npts values of the potential for this step.  Returns 0 or -1.
+ */
+int hjo_step_points_f64(int ndim, const int64_t *shape, const double *dx, double h, const double *P,
+                        const int64_t *W, const double *u, const double *V, int64_t npoints,
+                        const int64_t *points, double *out, int nthreads)
+{
+    hjo_geom g;
+    if (hjo_geom_init(&g, ndim, shape, dx, h, P, W)) { hjo_geom_free(&g); return -1; }
+    hjo_set_threads(nthreads);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < npoints; ++q) {
+        int64_t x = points[q];
+        if (x < 0 || x >= g.npts) { bad = 1; continue; }
+        int64_t y[HJO_MAXDIM];
+        int64_t rem = x;
+        for (int b = ndim - 1; b >= 0; --b) { y[b] = rem % g.shape[b]; rem /= g.shape[b]; }
+        double m = hjo_point_value(&g, u, ndim - 1, y);
+        if (V) m = m - h * V[x];
+        out[q] = m;
+    }
+    hjo_geom_free(&g);
+    return bad ? -1 : 0;
+}

@@ -63,6 +63,9 @@ def lib() -> ctypes.CDLL:
             L.hjo_adjoint_f64.argtypes = [i32, P(i64), P(f64), f64, P(f64), P(i64), P(f64),
                                           ctypes.c_void_p, i64, i64, P(f64), P(f64), P(f64),
                                           P(f64), i32]
+            L.hjo_step_points_f64.restype = i32
+            L.hjo_step_points_f64.argtypes = [i32, P(i64), P(f64), f64, P(f64), P(i64), P(f64),
+                                              ctypes.c_void_p, i64, P(i64), P(f64), i32]
             L.hjo_max_threads.restype = i32
             L.hjo_max_threads.argtypes = []
             _lib = L
@@ -142,6 +145,29 @@ def run(u0, dx, h, P, W, V=None, nsteps: int = 1, *, V_per_step: bool = False,
     if rc:
         raise ValueError("oracle rejected its arguments")
     return (u, amin) if record_argmin else u
+
+
+def step_points(u, dx, h, P, W, V, points, *, nthreads: int = 0):
+    """One binary64 step evaluated only at the given flat indices (sampling)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    ndim = u.ndim
+    shape = _vec(u.shape, ndim, np.int64)
+    dxv, Pv, Wv = _vec(dx, ndim, np.float64), _vec(P, ndim, np.float64), _vec(W, ndim, np.int64)
+    pts = np.ascontiguousarray(points, dtype=np.int64).ravel()
+    out = np.empty(pts.size, dtype=np.float64)
+    vptr = None
+    if V is not None:
+        Va = np.ascontiguousarray(V, dtype=np.float64)
+        if Va.shape != u.shape:
+            raise ValueError("V must have u's shape")
+        vptr = Va.ctypes.data
+    rc = lib().hjo_step_points_f64(ndim, _ptr(shape, ctypes.c_int64), _ptr(dxv, ctypes.c_double), float(h),
+                                   _ptr(Pv, ctypes.c_double), _ptr(Wv, ctypes.c_int64),
+                                   _ptr(u, ctypes.c_double), vptr, pts.size, _ptr(pts, ctypes.c_int64),
+                                   _ptr(out, ctypes.c_double), int(nthreads))
+    if rc:
+        raise ValueError("oracle rejected its arguments")
+    return out
 
 
 def adjoint(u0, dx, h, P, W, V, nsteps: int, ubar_n, *, V_per_step: bool = False, nthreads: int = 0):

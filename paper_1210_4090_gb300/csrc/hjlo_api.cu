@@ -1,0 +1,453 @@
+// hjlo_api.cu -- the C ABI declared in include/hjlo.h: plans, one step, the
+// time loop of eq. uN (replayed from a CUDA graph), the end-to-end host
+// variant, the effective-Hamiltonian readout of Prop. prop:klm and status.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "hjlo_internal.h"
+
+using namespace hjlo;
+
+namespace {
+
+constexpr int kGraphSteps = 16;  // steps per captured graph
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    const void *u = nullptr;
+    const double *hv = nullptr;
+};
+
+}  // namespace
+
+struct hjlo_plan {
+    hjlo_desc desc;
+    int ndim = 1;
+    int dtype = HJLO_F64;
+    int algo = HJLO_ALGO_MONGE;
+    long long npts = 1;
+    int esize = 8;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    AxisPlan ax[HJLO_MAX_DIM];
+    unsigned long long *d_counters = nullptr;  // CNT_N
+    int *d_flags = nullptr;
+    double *d_hv = nullptr;                    // npts, h*V of the current run
+    double *d_part = nullptr;                  // readout partials
+    void *d_u_host_run = nullptr;              // hjlo_run_host staging
+    double *d_V_host_run = nullptr;
+    GraphCache graph;
+    long long steps = 0;
+    int device = 0;
+};
+
+namespace {
+
+__global__ void scale_kernel(const double *__restrict__ V, double h, double *__restrict__ hv, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        hv[i] = __dmul_rn(h, V[i]);
+}
+
+constexpr int kReduceBlocks = 512;
+constexpr int kReduceThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double as_f64(T x) { return (double)x; }
+
+// Per-block partial (sum, min, max) of un - u0 in a fixed order; the second
+// kernel folds the partials in block order, so the readout is deterministic.
+template <typename T>
+__global__ void diff_partials(const T *__restrict__ u0, const T *__restrict__ un, long long n,
+                              double *__restrict__ part)
+{
+    __shared__ double ss[kReduceThreads], smn[kReduceThreads], smx[kReduceThreads];
+    double s = 0.0, mn = INFINITY, mx = -INFINITY;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double d = __dsub_rn(as_f64(un[i]), as_f64(u0[i]));
+        s = __dadd_rn(s, d);
+        mn = fmin(mn, d);
+        mx = fmax(mx, d);
+    }
+    ss[threadIdx.x] = s;
+    smn[threadIdx.x] = mn;
+    smx[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = kReduceThreads / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            ss[threadIdx.x] = __dadd_rn(ss[threadIdx.x], ss[threadIdx.x + o]);
+            smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + o]);
+            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = ss[0];
+        part[3 * blockIdx.x + 1] = smn[0];
+        part[3 * blockIdx.x + 2] = smx[0];
+    }
+}
+
+__global__ void fold_partials(double *part, int nblocks)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0, mn = INFINITY, mx = -INFINITY;
+    for (int b = 0; b < nblocks; ++b) {
+        s = __dadd_rn(s, part[3 * b]);
+        mn = fmin(mn, part[3 * b + 1]);
+        mx = fmax(mx, part[3 * b + 2]);
+    }
+    part[3 * nblocks + 0] = s;
+    part[3 * nblocks + 1] = mn;
+    part[3 * nblocks + 2] = mx;
+}
+
+hjlo_status check_plan(const hjlo_plan *p)
+{
+    if (!p) return set_error(HJLO_EINVAL, "plan is NULL");
+    return HJLO_OK;
+}
+
+hjlo_status set_device(const hjlo_plan *p)
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) {
+        cudaError_t e = cudaSetDevice(p->device);
+        if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+    }
+    return HJLO_OK;
+}
+
+// All passes of one step.  src -> dst for axis 0, then in place on dst.
+hjlo_status enqueue_step(hjlo_plan *p, const void *src, void *dst, const double *hv, double hv_scale,
+                         int32_t *amin, cudaStream_t st)
+{
+    for (int a = 0; a < p->ndim; ++a) {
+        const bool last = (a == p->ndim - 1);
+        hjlo_status s = launch_pass(p->ax[a], p->dtype, a == 0 ? src : dst, dst, last ? hv : nullptr,
+                                    last ? hv_scale : 0.0, amin ? amin + (long long)a * p->npts : nullptr,
+                                    p->d_counters, p->d_flags, st);
+        if (s != HJLO_OK) return s;
+    }
+    return HJLO_OK;
+}
+
+hjlo_status ensure_hv(hjlo_plan *p)
+{
+    if (p->d_hv) return HJLO_OK;
+    cudaError_t e = cudaMalloc(&p->d_hv, sizeof(double) * p->npts);
+    if (e != cudaSuccess) { p->d_hv = nullptr; return cuda_error(e, "cudaMalloc(h*V)"); }
+    return HJLO_OK;
+}
+
+hjlo_status form_hv(hjlo_plan *p, const double *V)
+{
+    hjlo_status s = ensure_hv(p);
+    if (s != HJLO_OK) return s;
+    long long blocks = std::min<long long>((p->npts + 255) / 256, 4096);
+    scale_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(V, p->desc.h, p->d_hv, p->npts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "h*V kernel launch");
+    return HJLO_OK;
+}
+
+bool ranges_overlap(const void *a, const void *b, size_t n)
+{
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
+}
+
+void destroy_graph(hjlo_plan *p)
+{
+    if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
+    p->graph = GraphCache();
+}
+
+hjlo_status capture_graph(hjlo_plan *p, void *u, const double *hv)
+{
+    destroy_graph(p);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+    hjlo_status s = HJLO_OK;
+    for (int k = 0; k < kGraphSteps && s == HJLO_OK; ++k) s = enqueue_step(p, u, u, hv, 0.0, nullptr, p->cap_stream);
+    e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (s != HJLO_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&p->graph.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { p->graph.exec = nullptr; return cuda_error(e, "cudaGraphInstantiate"); }
+    p->graph.u = u;
+    p->graph.hv = hv;
+    return HJLO_OK;
+}
+
+hjlo_status run_impl(hjlo_plan *p, void *u, const double *V, long long nsteps, bool tv)
+{
+    const double *hv = nullptr;
+    if (V && !tv) {
+        hjlo_status s = form_hv(p, V);
+        if (s != HJLO_OK) return s;
+        hv = p->d_hv;
+    }
+    long long n = 0;
+    if (!tv && nsteps >= 2 * kGraphSteps) {
+        if (!p->graph.exec || p->graph.u != u || p->graph.hv != hv) {
+            hjlo_status s = capture_graph(p, u, hv);
+            if (s != HJLO_OK) return s;
+        }
+        for (; n + kGraphSteps <= nsteps; n += kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(p->graph.exec, p->stream);
+            if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+        }
+    }
+    for (; n < nsteps; ++n) {
+        const double *v = tv ? (V ? V + n * p->npts : nullptr) : hv;
+        hjlo_status s = enqueue_step(p, u, u, v, tv ? p->desc.h : 0.0, nullptr, p->stream);
+        if (s != HJLO_OK) return s;
+    }
+    p->steps += nsteps;
+    return HJLO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t hjlo_version(void) { return HJLO_VERSION; }
+
+const char *hjlo_last_error(void) { return last_error_cstr(); }
+
+hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **out)
+{
+    if (!out) return set_error(HJLO_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d) return set_error(HJLO_EINVAL, "descriptor is NULL");
+    if (d->ndim < 1 || d->ndim > HJLO_MAX_DIM) return set_error(HJLO_EINVAL, "ndim must be 1..3");
+    if (d->dtype != HJLO_F64 && d->dtype != HJLO_F32_STORAGE) return set_error(HJLO_EINVAL, "unknown dtype");
+    if (d->algo < HJLO_ALGO_AUTO || d->algo > HJLO_ALGO_MONGE) return set_error(HJLO_EINVAL, "unknown algo");
+    if (d->reserved != 0) return set_error(HJLO_EINVAL, "reserved field must be 0");
+    if (!(d->h > 0) || !std::isfinite(d->h)) return set_error(HJLO_EINVAL, "h must be finite and > 0");
+    long long npts = 1;
+    for (int a = 0; a < d->ndim; ++a) {
+        if (d->shape[a] < 1) return set_error(HJLO_EINVAL, "shape[%d] must be >= 1", a);
+        if (d->shape[a] > (1LL << 24)) return set_error(HJLO_EUNSUPPORTED, "shape[%d] too large", a);
+        if (!(d->dx[a] > 0) || !std::isfinite(d->dx[a])) return set_error(HJLO_EINVAL, "dx[%d] must be > 0", a);
+        if (!std::isfinite(d->P[a])) return set_error(HJLO_EINVAL, "P[%d] must be finite", a);
+        npts *= d->shape[a];
+        if (npts > (1LL << 40)) return set_error(HJLO_EUNSUPPORTED, "grid too large");
+    }
+    DeviceFacts df;
+    hjlo_status s = device_facts(df);
+    if (s != HJLO_OK) return s;
+    if ((s = prepare_kernels()) != HJLO_OK) return s;
+
+    hjlo_plan *p = new (std::nothrow) hjlo_plan();
+    if (!p) return set_error(HJLO_ENOMEM, "host allocation");
+    p->desc = *d;
+    p->ndim = d->ndim;
+    p->dtype = d->dtype;
+    p->npts = npts;
+    p->esize = (d->dtype == HJLO_F64) ? 8 : 4;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->device = df.device;
+    bool all_monge = true;
+    for (int a = 0; a < p->ndim; ++a) {
+        AxisPlan &ax = p->ax[a];
+        long long inner = 1, outer = 1;
+        for (int b = 0; b < a; ++b) outer *= d->shape[b];
+        for (int b = a + 1; b < p->ndim; ++b) inner *= d->shape[b];
+        ax.inner = inner;
+        ax.outer = outer;
+        double *k64 = nullptr;
+        s = resolve_axis(d->shape[a], d->dx[a], d->h, d->P[a], d->window[a], ax, &k64);
+        if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
+        int algo = KALGO_MONGE;
+        if (d->algo == HJLO_ALGO_BRUTE) algo = KALGO_BRUTE;
+        if (d->algo == HJLO_ALGO_AUTO && (ax.weff < 8 || !(ax.curv > 0))) algo = KALGO_BRUTE;
+        if (algo != KALGO_MONGE) all_monge = false;
+        s = shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
+        if (s == HJLO_OK) {
+            cudaError_t e = cudaMalloc(&ax.d_kr64, sizeof(double) * ax.weff);
+            if (e == cudaSuccess) e = cudaMemcpy(ax.d_kr64, k64, sizeof(double) * ax.weff, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) s = cuda_error(e, "kernel table upload");
+        }
+        free(k64);
+        if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
+    }
+    p->algo = all_monge ? HJLO_ALGO_MONGE : HJLO_ALGO_BRUTE;
+    cudaError_t e = cudaMalloc(&p->d_counters, sizeof(unsigned long long) * CNT_N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_flags, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_counters, 0, sizeof(unsigned long long) * CNT_N);
+    if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { s = cuda_error(e, "plan allocation"); hjlo_plan_destroy(p); return s; }
+    *out = p;
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_plan_destroy(hjlo_plan *p)
+{
+    if (!p) return HJLO_OK;
+    set_device(p);
+    if (p->stream || p->cap_stream) cudaStreamSynchronize(p->stream);
+    destroy_graph(p);
+    for (int a = 0; a < HJLO_MAX_DIM; ++a) {
+        cudaFree(p->ax[a].d_kr64);
+    }
+    cudaFree(p->d_counters);
+    cudaFree(p->d_flags);
+    cudaFree(p->d_hv);
+    cudaFree(p->d_part);
+    cudaFree(p->d_u_host_run);
+    cudaFree(p->d_V_host_run);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    delete p;
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_plan_info(const hjlo_plan *p, hjlo_plan_facts *info)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!info) return set_error(HJLO_EINVAL, "info is NULL");
+    memset(info, 0, sizeof(*info));
+    info->ndim = p->ndim;
+    info->algo = p->algo;
+    info->npts = p->npts;
+    for (int a = 0; a < p->ndim; ++a) {
+        info->dlo[a] = p->ax[a].dlo;
+        info->dhi[a] = p->ax[a].dhi;
+        info->centre[a] = p->ax[a].centre;
+        info->kmin[a] = p->ax[a].kmin;
+        info->curvature[a] = p->ax[a].curv;
+    }
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_step(hjlo_plan *p, const void *u_in, void *u_out, const double *V, int32_t *argmin_out)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!u_in || !u_out) return set_error(HJLO_EINVAL, "u_in/u_out is NULL");
+    const size_t bytes = (size_t)p->npts * p->esize;
+    if (u_in != u_out && ranges_overlap(u_in, u_out, bytes))
+        return set_error(HJLO_EINVAL, "u_in and u_out overlap without being equal");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    const double *hv = nullptr;
+    if (V) {
+        if ((s = form_hv(p, V)) != HJLO_OK) return s;
+        hv = p->d_hv;
+    }
+    s = enqueue_step(p, u_in, u_out, hv, 0.0, argmin_out, p->stream);
+    if (s == HJLO_OK) p->steps += 1;
+    return s;
+}
+
+hjlo_status hjlo_run(hjlo_plan *p, void *u, const double *V, int64_t nsteps)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!u) return set_error(HJLO_EINVAL, "u is NULL");
+    if (nsteps < 0) return set_error(HJLO_EINVAL, "nsteps must be >= 0");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    return run_impl(p, u, V, nsteps, false);
+}
+
+hjlo_status hjlo_run_tv(hjlo_plan *p, void *u, const double *V, int64_t nsteps)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!u) return set_error(HJLO_EINVAL, "u is NULL");
+    if (nsteps < 0) return set_error(HJLO_EINVAL, "nsteps must be >= 0");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    return run_impl(p, u, V, nsteps, true);
+}
+
+hjlo_status hjlo_run_host(hjlo_plan *p, void *u_host, const double *V_host, int64_t nsteps)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!u_host) return set_error(HJLO_EINVAL, "u_host is NULL");
+    if (nsteps < 0) return set_error(HJLO_EINVAL, "nsteps must be >= 0");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    const size_t ub = (size_t)p->npts * p->esize, vb = (size_t)p->npts * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (!p->d_u_host_run) e = cudaMalloc(&p->d_u_host_run, ub);
+    if (e == cudaSuccess && V_host && !p->d_V_host_run) e = cudaMalloc(&p->d_V_host_run, vb);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(host-run buffers)");
+    e = cudaMemcpyAsync(p->d_u_host_run, u_host, ub, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && V_host) e = cudaMemcpyAsync(p->d_V_host_run, V_host, vb, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(H2D)");
+    s = run_impl(p, p->d_u_host_run, V_host ? p->d_V_host_run : nullptr, nsteps, false);
+    if (s != HJLO_OK) return s;
+    e = cudaMemcpyAsync(u_host, p->d_u_host_run, ub, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(D2H)");
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_hbar(hjlo_plan *p, const void *u0, const void *un, int64_t nsteps, double *out3)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!u0 || !un || !out3) return set_error(HJLO_EINVAL, "NULL argument");
+    if (nsteps < 1) return set_error(HJLO_EINVAL, "nsteps must be >= 1");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (!p->d_part) e = cudaMalloc(&p->d_part, sizeof(double) * 3 * (kReduceBlocks + 1));
+    if (e != cudaSuccess) { p->d_part = nullptr; return cuda_error(e, "cudaMalloc(readout)"); }
+    if (p->dtype == HJLO_F64)
+        diff_partials<double><<<kReduceBlocks, kReduceThreads, 0, p->stream>>>(
+            (const double *)u0, (const double *)un, p->npts, p->d_part);
+    else
+        diff_partials<float><<<kReduceBlocks, kReduceThreads, 0, p->stream>>>(
+            (const float *)u0, (const float *)un, p->npts, p->d_part);
+    fold_partials<<<1, 32, 0, p->stream>>>(p->d_part, kReduceBlocks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "readout kernels");
+    double r[3];
+    e = cudaMemcpyAsync(r, p->d_part + 3 * kReduceBlocks, sizeof(r), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_error(e, "readout copy");
+    const double T = (double)nsteps * p->desc.h;
+    out3[0] = -(r[0] / (double)p->npts) / T;
+    out3[1] = -r[2] / T;
+    out3[2] = -r[1] / T;
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_sync(hjlo_plan *p, hjlo_counters *out)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    unsigned long long c[CNT_N];
+    int flags = 0;
+    e = cudaMemcpy(c, p->d_counters, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&flags, p->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "counter copy");
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->exact_rescans = (int64_t)c[CNT_RESCAN];
+        out->brute_fallback_lines = (int64_t)c[CNT_FALLBACK];
+        out->steps = p->steps;
+        out->error_flags = flags;
+    }
+    if (flags) {
+        cudaMemset(p->d_flags, 0, sizeof(int));
+        if (flags & FLAG_TIMEOUT) return set_error(HJLO_ETIMEOUT, "a bounded device wait gave up");
+        return set_error(HJLO_EPRECOND, "a device precondition failed");
+    }
+    return HJLO_OK;
+}
+
+}  // extern "C"

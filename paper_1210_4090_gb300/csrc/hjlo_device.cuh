@@ -1,0 +1,704 @@
+// hjlo_device.cuh -- device code of the axis pass (one min-plus convolution
+// along one axis of the grid, Remark rk28 of Bouillard, Faou & Zavidovique,
+// with the potential term of eq. eqconvol fused into the last axis).
+//
+// A CTA owns a tile of C lines x N positions.  It stages the tile in shared
+// memory (TMA: one bulk copy for lines along the contiguous axis, a 3D tensor
+// copy for lines along a strided axis), finds for every output i the argmin
+// offset t (displacement d = dhi - t) and then writes
+//     m_i = fl(u[(i-d) mod N] + k[d])          (one binary64 add)
+//     u'_i = fl(m_i - hV_i)                    (last axis only)
+// so each output costs exactly the binary64 operations of the definition.
+//
+// Halo index space.  For row i the window of lifted sources j = i - d,
+// d in [dlo, dhi], is shifted to jj = j + dhi in [i, i + weff - 1]; the source
+// position is (jj + hoff) mod N with hoff = (-dhi) mod N, and the kernel entry
+// is kr[jj - i] = k[dhi - (jj - i)] (the table stored reversed).  Ascending jj
+// is ascending lifted source, so a strict '<' scan keeps the smallest source
+// among equal values (the library's tie rule).
+//
+// MONGE search.  u[j] + k[i-j] is a Monge matrix with margin
+// a = min second difference of k > 0 (k convex, hypothesis (i)): the leftmost
+// row argmin is non-decreasing in i, and along the periodic line
+// argmin(i+N) = argmin(i) + N.  Lane g of the line's lpl lanes owns the rows
+// [s_g, s_{g+1}), s_g = min(g*S, N) with S odd (so that lanes reading rows S
+// apart fall in different shared-memory banks): it scans the whole window for
+// its first row (the pivot) and then fills its segment by divide and conquer,
+// each row searching only between the argmins of two rows already known.  Every
+// comparison is made first on an int32 fixed-point screen: per line,
+// (u - min u)/2^q and k/2^q truncated, 2^q chosen so that the line's range
+// fills 29 bits; each screened candidate is within 3 units of the exact sum.
+// When another candidate lies within 6 units (+ one binary64 ulp of the
+// values, in units) of the screened minimum, the row is re-scanned in binary64
+// over the surviving candidates, so the argmin (and the value) is the binary64
+// one.  Ties in binary64 sit within the bracket as long as
+// a > 8 ulp(max|u| + max|k|); a line that fails this margin (or holds
+// non-finite values) is handed to the brute-force scan.  The conversions use
+// integer instructions only: on this part the binary64 pipe is the scarce
+// unit, and it is kept for the one add per output of the definition.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hjlo {
+
+enum { LAYOUT_CONTIG = 0, LAYOUT_STRIDED = 1 };
+enum { KALGO_BRUTE = 1, KALGO_MONGE = 2 };
+enum { FLAG_PRECOND = 1, FLAG_TIMEOUT = 2 };
+enum { CNT_RESCAN = 0, CNT_FALLBACK = 1, CNT_N = 4 };
+
+struct PassParams {
+    const void *src;          // tile source (global)
+    void *dst;                // output (global); may equal src
+    const double *hv;         // h*V for the potential term, or nullptr
+    int32_t *amin;            // argmin displacement d per point, or nullptr
+    const double *kr64;       // kr64[t] = k[dhi - t], t in [0, weff)
+    unsigned long long *counters;
+    int *flags;
+    long long N, inner, outer;
+    long long ntiles;
+    long long tiles_per_outer;  // STRIDED: ceil(inner / C)
+    int hoff;                 // (-dhi) mod N
+    int dhi;                  // argmin output: d = dhi - t
+    int weff;                 // window size (<= N)
+    int C, log2C;             // lines per tile (power of two)
+    int wpl;                  // BRUTE: warps per line
+    int lpl, log2lpl;         // MONGE: lanes per line (power of two)
+    int seg;                  // MONGE: rows per lane segment (odd)
+    int gs;                   // MONGE: lanes sharing one full-window pivot scan (power of two <= 32)
+    int tp;                   // pitch (uint16) of a line's argmin offsets; tp % 4 == 2
+    int use_tma;
+    int by, nbox;             // STRIDED TMA: rows per box, boxes per tile
+    int lp;                   // pitch (int32 words) of a line in the fixed-point halo
+    double kmax;              // max |k| over the window
+    double curv;              // lower bound of the min second difference of k (inf if weff < 3)
+    int off_u, off_fx, off_kfx, off_t, off_k64, off_misc;  // shared memory offsets (bytes)
+    long long wait_ns;        // bound on every mbarrier wait
+    double hscale;            // hv_scaled: potential term fl(m - fl(hscale * hv[x]))
+    int hv_scaled;            // 0: hv already holds h*V
+};
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier for at most `limit_ns`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit_ns)
+{
+    unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((long long)(global_ns() - t0) > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_tensor_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                                   uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------------ number helpers
+
+// Order-preserving integer key of a binary64 value; -0 maps to +0's key so
+// that equal values (IEEE ==) have equal keys.  Finite inputs only.
+__device__ __forceinline__ unsigned long long dkey(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    return (b == 0x8000000000000000ull) ? 0x8000000000000000ull : k;
+}
+
+// Inverse of dkey for keys of finite values.
+__device__ __forceinline__ double dkey_decode(unsigned long long k)
+{
+    unsigned long long b = (k >> 63) ? (k ^ 0x8000000000000000ull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// Unbiased binary exponent of |x| (x finite, nonzero normal or subnormal).
+__device__ __forceinline__ int expo(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int eb = (int)((b >> 52) & 0x7ff);
+    return (eb ? eb : 1) - 1023;
+}
+
+// x / 2^q truncated toward zero, modulo 2^32 (two's complement), with 32-bit
+// integer instructions only.  The difference of two such values is exact
+// modulo 2^32 up to the two truncations (each below one unit), so it is
+// correct whenever the true difference fits in an int32 -- however large
+// |x| / 2^q itself is.
+__device__ __forceinline__ unsigned fixq32(double x, int q)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    int eb = (int)((hi >> 20) & 0x7ffu);
+    unsigned mh = (hi & 0xfffffu) | (eb ? 0x100000u : 0u);    // significand = mh:lo (53 bits)
+    int s = (eb ? eb : 1) - 1075 - q;                          // |x| / 2^q = significand * 2^s
+    unsigned v;
+    if (s >= 0) {
+        v = (s < 32) ? (lo << s) : 0u;
+    } else {
+        int k = -s;
+        v = (k < 32) ? __funnelshift_r(lo, mh, k) : ((k < 64) ? (mh >> (k - 32)) : 0u);
+    }
+    unsigned sg = (unsigned)((int)hi >> 31);
+    return (v ^ sg) - sg;
+}
+
+// Exact binary32 -> binary64 (integer ops for normal numbers).
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x)
+{
+    unsigned b = __float_as_uint(x);
+    unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;   // zero, subnormal, inf, nan
+    unsigned long long r = ((unsigned long long)(b & 0x80000000u) << 32) |
+                           ((unsigned long long)(e - 127u + 1023u) << 52) |
+                           ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)r);
+}
+
+__device__ __forceinline__ void store_val(double *p, double m) { *p = m; }
+__device__ __forceinline__ void store_val(float *p, double m) { *p = __double2float_rn(m); }
+
+// Order-preserving int32 key of the high word of a binary64 value: keys of
+// two values compare like the values, up to the discarded low word.
+__device__ __forceinline__ int hikey(double x)
+{
+    int hi = (int)((unsigned long long)__double_as_longlong(x) >> 32);
+    return hi ^ ((hi >> 31) & 0x7fffffff);
+}
+
+// A binary64 bound from a high-word key: the smallest (lower = true) or the
+// largest value whose high word has this key.
+__device__ __forceinline__ double hikey_bound(int key, bool lower)
+{
+    int hi = key ^ ((key >> 31) & 0x7fffffff);
+    bool neg = hi < 0;
+    unsigned lo = (neg == lower) ? 0xffffffffu : 0u;
+    unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | lo;
+    return __longlong_as_double((long long)b);
+}
+
+// ------------------------------------------------------------------ tile geometry
+
+template <int LAYOUT>
+struct Tile {
+    long long base;     // global element index of (line 0, position 0)
+    long long lstride;  // global stride between lines of the tile
+    long long pstride;  // global stride between positions of a line
+    int valid;          // lines of the tile that exist
+};
+
+template <int LAYOUT>
+__device__ __forceinline__ Tile<LAYOUT> tile_of(const PassParams &p, long long tile)
+{
+    Tile<LAYOUT> t;
+    if (LAYOUT == LAYOUT_CONTIG) {
+        long long l0 = tile << p.log2C;
+        t.base = l0 * p.N;
+        t.lstride = p.N;
+        t.pstride = 1;
+        long long rem = p.outer - l0;
+        t.valid = (int)(rem < p.C ? rem : p.C);
+    } else {
+        long long o = tile / p.tiles_per_outer;
+        long long in0 = (tile - o * p.tiles_per_outer) << p.log2C;
+        t.base = o * p.N * p.inner + in0;
+        t.lstride = 1;
+        t.pstride = p.inner;
+        long long rem = p.inner - in0;
+        t.valid = (int)(rem < p.C ? rem : p.C);
+    }
+    return t;
+}
+
+// shared-memory index of (line l, position i) in the staged tile
+template <int LAYOUT>
+__device__ __forceinline__ int uidx(const PassParams &p, int l, int i)
+{
+    return (LAYOUT == LAYOUT_CONTIG) ? (l * (int)p.N + i) : ((i << p.log2C) + l);
+}
+
+__device__ __forceinline__ int wrapN(int x, int N)
+{
+    x = (x >= N) ? x - N : x;
+    return (x >= N) ? x - N : x;
+}
+
+// Exact scan of halo indices [lo, hi] for row r: smallest key, ascending jj.
+template <typename T, int LAYOUT>
+__device__ __forceinline__ void exact_scan(const PassParams &p, const T *su, const double *kr64, int l, int r,
+                                           int lo, int hi, unsigned long long &best, int &bt)
+{
+    const int N = (int)p.N;
+    int pos = wrapN(lo + p.hoff, N);
+    for (int jj = lo; jj <= hi; ++jj) {
+        double c = __dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[jj - r]);
+        unsigned long long key = dkey(c);
+        if (key < best) { best = key; bt = jj - r; }
+        pos = (pos + 1 == N) ? 0 : pos + 1;
+    }
+}
+
+// Screened search of row r over the offsets t in [tlo, thi] (halo index
+// r + t); f = the line's fixed-point halo shifted to row r, k = the line's
+// fixed-point kernel table.  Returns the argmin offset t.  `rescans` counts
+// rows that needed the binary64 re-scan.
+template <typename T, int LAYOUT>
+__device__ __forceinline__ int screened_row(const PassParams &p, const T *su, const int *f, const int *k,
+                                            const double *kr64, int l, int r, int tlo, int thi, int thr_add,
+                                            int &rescans)
+{
+    int m1 = 0x7fffffff, m2 = 0x7fffffff, t1 = tlo;
+#pragma unroll 4
+    for (int t = tlo; t <= thi; ++t) {
+        int c = f[t] + k[t];
+        m2 = min(m2, max(m1, c));
+        t1 = (c < m1) ? t : t1;
+        m1 = min(m1, c);
+    }
+    const int thr = m1 + thr_add;
+    if (m2 > thr) return t1;
+    // another candidate is within the screen's error: binary64 over the survivors
+    ++rescans;
+    const int N = (int)p.N;
+    unsigned long long best = ~0ull;
+    int bt = t1;
+    for (int t = tlo; t <= thi; ++t) {
+        int c = f[t] + k[t];
+        if (c <= thr) {
+            int pos = wrapN(r + t + p.hoff, N);
+            double e = __dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[t]);
+            unsigned long long key = dkey(e);
+            if (key < best) { best = key; bt = t; }
+        }
+    }
+    return bt;
+}
+
+// One output: the binary64 add of the kept candidate, the potential term and
+// the stores.
+template <typename T, int LAYOUT>
+__device__ __forceinline__ void finish_point(const PassParams &p, const Tile<LAYOUT> &tl, const T *su,
+                                             const unsigned short *tt, const double *kr64, T *dst, int l, int i)
+{
+    const int N = (int)p.N;
+    int t = tt[l * p.tp + i];
+    int pos = wrapN(i + t + p.hoff, N);
+    double m = __dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[t]);
+    long long x = tl.base + l * tl.lstride + (long long)i * tl.pstride;
+    if (p.hv) {
+        double hv = p.hv_scaled ? __dmul_rn(p.hscale, p.hv[x]) : p.hv[x];
+        m = __dsub_rn(m, hv);
+    }
+    store_val(dst + x, m);
+    if (p.amin) p.amin[x] = p.dhi - t;
+}
+
+// ------------------------------------------------------------------ the pass kernel
+
+// Per-line facts of the fixed-point screen, in shared memory.
+struct LineInfo {
+    unsigned fref;                  // fixq32(lower bound of u, q)
+    int pad0;
+    int kmin, kmax;                 // hikey of min u and max u over the line
+    int q;                          // unit 2^q
+    int thr_add;                    // survivors: screened value <= min + thr_add
+    int fallback;                   // 1: brute force for this line
+    int pad;
+};
+
+template <typename T, int LAYOUT, int ALGO>
+__global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUtensorMap tmap, PassParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    T *su = reinterpret_cast<T *>(smem + p.off_u);
+    int *fx = reinterpret_cast<int *>(smem + p.off_fx);
+    int *kfx = reinterpret_cast<int *>(smem + p.off_kfx);
+    unsigned short *tt = reinterpret_cast<unsigned short *>(smem + p.off_t);
+    double *kr64 = reinterpret_cast<double *>(smem + p.off_k64);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + p.off_misc);
+    int *scnt = reinterpret_cast<int *>(smem + p.off_misc + 8);                  // [2]
+    LineInfo *li = reinterpret_cast<LineInfo *>(smem + p.off_misc + 16);         // [C]
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int N = (int)p.N, C = p.C, weff = p.weff;
+    const long long tile = blockIdx.x;
+    if (tile >= p.ntiles) return;
+    const Tile<LAYOUT> tl = tile_of<LAYOUT>(p, tile);
+    const T *src = reinterpret_cast<const T *>(p.src);
+
+    // ---- stage the tile
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        scnt[0] = 0;
+        scnt[1] = 0;
+    }
+    if (ALGO == KALGO_MONGE && tid < C) {
+        li[tid].kmin = 0x7fffffff;
+        li[tid].kmax = (int)0x80000000;
+    }
+    __syncthreads();
+    if (p.use_tma) {
+        if (tid == 0) {
+            if (LAYOUT == LAYOUT_CONTIG) {
+                uint32_t bytes = (uint32_t)((long long)tl.valid * N * (long long)sizeof(T));
+                mbar_arrive_expect_tx(bar, bytes);
+                tma_bulk_load(su, src + tl.base, bytes, bar);
+            } else {
+                uint32_t bytes = (uint32_t)(p.nbox * p.by * C * (int)sizeof(T));
+                mbar_arrive_expect_tx(bar, bytes);
+                long long o = tile / p.tiles_per_outer;
+                int x0 = (int)((tile - o * p.tiles_per_outer) << p.log2C);
+                for (int b = 0; b < p.nbox; ++b)
+                    tma_tensor_load_3d(su + (long long)b * p.by * C, &tmap, x0, b * p.by, (int)o, bar);
+            }
+        }
+    } else {
+        for (int l = 0; l < tl.valid; ++l)
+            for (int i = tid; i < N; i += nthr)
+                su[uidx<LAYOUT>(p, l, i)] = src[tl.base + l * tl.lstride + (long long)i * tl.pstride];
+    }
+    for (int i = tid; i < weff; i += nthr) kr64[i] = p.kr64[i];
+    if (p.use_tma) {
+        bool ok = mbar_wait_bounded(bar, 0, p.wait_ns);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not land in time: flag it, give it one more bounded
+            // wait so nothing is still writing our shared memory, and leave
+            if (tid == 0) atomicOr(p.flags, FLAG_TIMEOUT);
+            mbar_wait_bounded(bar, 0, p.wait_ns);
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
+
+    const int lane = tid & 31, warp = tid >> 5;
+
+    if (ALGO == KALGO_MONGE) {
+        const int lpl = p.lpl;
+        // line-major thread groups for the contiguous layout: lpl consecutive
+        // threads per line (nthr = C * lpl)
+        const int cl = tid >> p.log2lpl, sub = tid & (lpl - 1);
+        // ---- per-line range from high-word keys (integer instructions only)
+        {
+            int mn = 0x7fffffff, mx = (int)0x80000000;
+            if (LAYOUT == LAYOUT_CONTIG) {
+                if (cl < tl.valid)
+                    for (int i = sub; i < N; i += lpl) {
+                        int k = hikey(widen(su[cl * N + i]));
+                        mn = min(mn, k);
+                        mx = max(mx, k);
+                    }
+                const int lim = lpl < 32 ? lpl : 32;
+                for (int o = lim >> 1; o; o >>= 1) {
+                    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                }
+                if ((lane & (lim - 1)) == 0 && cl < tl.valid) {
+                    atomicMin(&li[cl].kmin, mn);
+                    atomicMax(&li[cl].kmax, mx);
+                }
+            } else {
+                // line index fastest: consecutive threads read consecutive
+                // words; each thread keeps one line (nthr is a multiple of C)
+                const int l = tid & (C - 1);
+                for (int idx = tid; idx < C * N; idx += nthr) {
+                    int k = hikey(widen(su[idx]));
+                    mn = min(mn, k);
+                    mx = max(mx, k);
+                }
+                for (int o = 16; o >= C; o >>= 1) {
+                    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                }
+                if (lane < C && l < tl.valid) {
+                    atomicMin(&li[l].kmin, mn);
+                    atomicMax(&li[l].kmax, mx);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- per-line scale, survivor threshold and Monge margin
+        if (tid < tl.valid) {
+            LineInfo &L = li[tid];
+            const double umin = hikey_bound(L.kmin, true), umax = hikey_bound(L.kmax, false);
+            const double R = __dsub_ru(umax, umin);
+            const double Rk = __dadd_ru(R, __dmul_ru(2.0, p.kmax));
+            const double cmax = __dadd_ru(fmax(fabs(umin), fabs(umax)), p.kmax);
+            const bool finite = isfinite(Rk) && isfinite(cmax);
+            const int q = (finite && Rk > 0.0) ? expo(Rk) - 28 : -1074;
+            int tie = finite ? expo(cmax) - 52 - q : 0;
+            tie = tie < 0 ? 0 : (tie > 28 ? 28 : tie);
+            L.q = q;
+            L.fref = fixq32(umin, q);
+            L.thr_add = 7 + (1 << tie);
+            L.fallback = (!finite || !(p.curv > __dmul_ru(cmax, 0x1p-49))) ? 1 : 0;
+        }
+        __syncthreads();
+        // ---- fixed-point halo of every line and the line's kernel table
+        const int L = N + weff - 1;
+        if (LAYOUT == LAYOUT_CONTIG) {
+            if (cl < tl.valid) {
+                const int q = li[cl].q;
+                const unsigned fref = li[cl].fref;
+                int *lfx = fx + cl * p.lp;
+                const T *lu = su + cl * N;
+                int pos = (sub + p.hoff) % N;
+                for (int jj = sub; jj < L; jj += lpl) {
+                    lfx[jj] = (int)(fixq32(widen(lu[pos]), q) - fref);
+                    pos += lpl;
+                    while (pos >= N) pos -= N;
+                }
+                for (int t = sub; t < weff; t += lpl) kfx[cl * weff + t] = (int)fixq32(kr64[t], q);
+            }
+        } else {
+            const int l = tid & (C - 1);
+            if (l < tl.valid) {
+                const int q = li[l].q;
+                const unsigned fref = li[l].fref;
+                const int step = nthr >> p.log2C;
+                for (int jj = tid >> p.log2C; jj < L; jj += step) {
+                    int pos = wrapN(jj + p.hoff, N);
+                    fx[l * p.lp + jj] = (int)(fixq32(widen(su[(pos << p.log2C) + l]), q) - fref);
+                }
+                for (int t = tid >> p.log2C; t < weff; t += step) kfx[l * weff + t] = (int)fixq32(kr64[t], q);
+            }
+        }
+        __syncthreads();
+        // ---- monotone search: lane g of line `line` owns rows [s0, s1).
+        // Every barrier and shuffle below is reached by all threads of the
+        // block; the work between them is predicated per thread (lines of one
+        // warp may differ in validity and in fallback).
+        const int line = cl;
+        const int g = sub;
+        const bool active = line < tl.valid;
+        const int lsafe = active ? line : 0;
+        const int thr_add = li[lsafe].thr_add;
+        const bool fallback = li[lsafe].fallback != 0;
+        const int *lfx = fx + lsafe * p.lp;
+        const int *lk = kfx + lsafe * weff;
+        unsigned short *lt = tt + lsafe * p.tp;
+        const bool work = active && !fallback;
+        int rescans = 0;
+        const int S = p.seg, GS = p.gs;
+        const int s0 = min(g * S, N), s1 = min((g + 1) * S, N);
+        const int o = g & (GS - 1);
+        const int rp = min((g - o) * S, N);   // the group's pivot row
+        if (active && fallback) {
+            // brute force, one row per lane of the line
+            for (int r = g; r < N; r += lpl) {
+                unsigned long long best = ~0ull;
+                int bt = 0;
+                exact_scan<T, LAYOUT>(p, su, kr64, line, r, r, r + weff - 1, best, bt);
+                lt[r] = (unsigned short)bt;
+            }
+            if (g == 0) atomicAdd(&scnt[1], 1);
+        }
+        if (GS == 1) {
+            // P1: every segment's first row scans the whole window
+            if (work && s0 < s1)
+                lt[s0] = (unsigned short)screened_row<T, LAYOUT>(p, su, lfx + s0, lk, kr64, line, s0, 0, weff - 1,
+                                                                thr_add, rescans);
+            __syncthreads();
+        } else {
+            // P1: the GS lanes of a group share the whole-window scan of the
+            // group's first row; partial minima merge by shuffles
+            const int ch = (weff + GS - 1) / GS;
+            const int tlo = o * ch, thi = min(tlo + ch, weff) - 1;
+            const bool hp = work && rp < N;
+            int m1 = 0x7fffffff, m2 = 0x7fffffff, t1 = 0x7fffffff;
+            if (hp) {
+                const int *f = lfx + rp;
+#pragma unroll 4
+                for (int t = tlo; t <= thi; ++t) {
+                    int c = f[t] + lk[t];
+                    m2 = min(m2, max(m1, c));
+                    t1 = (c < m1) ? t : t1;
+                    m1 = min(m1, c);
+                }
+            }
+            for (int w = 1; w < GS; w <<= 1) {
+                int om1 = __shfl_xor_sync(0xffffffffu, m1, w);
+                int om2 = __shfl_xor_sync(0xffffffffu, m2, w);
+                int ot1 = __shfl_xor_sync(0xffffffffu, t1, w);
+                int nm2 = min(max(m1, om1), min(m2, om2));
+                if (om1 < m1 || (om1 == m1 && ot1 < t1)) { m1 = om1; t1 = ot1; }
+                m2 = nm2;
+            }
+            const int thr = hp ? m1 + thr_add : 0;
+            const bool need = hp && !(m2 > thr);
+            int tpiv = t1;
+            if (__any_sync(0xffffffffu, need)) {
+                unsigned long long bk = ~0ull;
+                int bt = 0x7fffffff;
+                if (need) {
+                    const int *f = lfx + rp;
+                    for (int t = tlo; t <= thi; ++t) {
+                        if (f[t] + lk[t] <= thr) {
+                            int pos = wrapN(rp + t + p.hoff, N);
+                            double e = __dadd_rn(widen(su[uidx<LAYOUT>(p, line, pos)]), kr64[t]);
+                            unsigned long long key = dkey(e);
+                            if (key < bk) { bk = key; bt = t; }
+                        }
+                    }
+                }
+                for (int w = 1; w < GS; w <<= 1) {
+                    unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, w);
+                    int ot = __shfl_xor_sync(0xffffffffu, bt, w);
+                    if (ok < bk || (ok == bk && ot < bt)) { bk = ok; bt = ot; }
+                }
+                if (need) tpiv = bt;
+                if (need && o == 0) ++rescans;
+            }
+            if (hp && o == 0) lt[rp] = (unsigned short)tpiv;
+            __syncthreads();
+            // P2: the other segments' first rows, bracketed by the argmins of
+            // this group's and the next group's pivot rows
+            if (work && o != 0 && s0 < s1) {
+                const int jl = rp + lt[rp];
+                const int rn = min((g - o + GS) * S, N);
+                const int jr = (rn < N) ? rn + lt[rn] : N + lt[0];
+                int lo = max(jl - s0, 0), hi = min(jr - s0, weff - 1);
+                if (lo > hi) { lo = 0; hi = weff - 1; }   // never for a Monge matrix
+                lt[s0] = (unsigned short)screened_row<T, LAYOUT>(p, su, lfx + s0, lk, kr64, line, s0, lo, hi,
+                                                                thr_add, rescans);
+            }
+            __syncthreads();
+        }
+        // P3: the rest of each segment by divide and conquer
+        if (work && s1 - s0 >= 2) {
+            // right bracket: the next segment's first row, or the first row
+            // shifted by one period
+            const int jnext = (s1 < N) ? (s1 + lt[s1]) : (N + lt[0]);
+            const int Sg = s1 - s0;
+            int step = 1;
+            while (step * 2 < Sg) step *= 2;
+            for (; step >= 1; step >>= 1) {
+                for (int r = s0 + step; r < s1; r += 2 * step) {
+                    int jl = (r - step) + lt[r - step];
+                    int qq = r + step;
+                    int jr = (qq < s1) ? qq + lt[qq] : jnext;
+                    int tlo = max(jl - r, 0), thi = min(jr - r, weff - 1);
+                    if (tlo > thi) { tlo = 0; thi = weff - 1; }   // never for a Monge matrix
+                    lt[r] = (unsigned short)screened_row<T, LAYOUT>(p, su, lfx + r, lk, kr64, line, r, tlo, thi,
+                                                                   thr_add, rescans);
+                }
+            }
+        }
+        if (rescans) atomicAdd(&scnt[0], rescans);
+    } else {
+        // ---- brute force: every row scanned by a whole warp, shuffle reduction
+        const int line = warp / p.wpl;
+        if (line < tl.valid) {
+            unsigned short *lt = tt + line * p.tp;
+            const int wl = warp - line * p.wpl;
+            for (int r = wl; r < N; r += p.wpl) {
+                unsigned long long best = ~0ull;
+                int bt = 0;
+                const int lo = r + lane, hi = r + weff - 1;
+                if (lo <= hi) {
+                    int pos = wrapN(lo + p.hoff, N);
+                    for (int jj = lo; jj <= hi; jj += 32) {
+                        double c = __dadd_rn(widen(su[uidx<LAYOUT>(p, line, pos)]), kr64[jj - r]);
+                        unsigned long long key = dkey(c);
+                        if (key < best) { best = key; bt = jj - r; }
+                        pos += 32;
+                        while (pos >= N) pos -= N;
+                    }
+                }
+                for (int o = 16; o; o >>= 1) {
+                    unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+                    int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                    if (ok < best || (ok == best && ot < bt)) { best = ok; bt = ot; }
+                }
+                if (lane == 0) lt[r] = (unsigned short)bt;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- exact values, potential term, stores (coalesced order)
+    T *dst = reinterpret_cast<T *>(p.dst);
+    if (LAYOUT == LAYOUT_CONTIG) {
+        const int lanes = nthr >> p.log2C;              // threads per line
+        const int l = tid / lanes, sub = tid - l * lanes;
+        if (l < tl.valid)
+            for (int i = sub; i < N; i += lanes) finish_point<T, LAYOUT>(p, tl, su, tt, kr64, dst, l, i);
+    } else {
+        const int total = C * N;
+        for (int idx = tid; idx < total; idx += nthr) {
+            int i = idx >> p.log2C, l = idx & (C - 1);
+            if (l < tl.valid) finish_point<T, LAYOUT>(p, tl, su, tt, kr64, dst, l, i);
+        }
+    }
+    if (ALGO == KALGO_MONGE && tid == 0) {
+        if (scnt[0]) atomicAdd(&p.counters[CNT_RESCAN], (unsigned long long)scnt[0]);
+        if (scnt[1]) atomicAdd(&p.counters[CNT_FALLBACK], (unsigned long long)scnt[1]);
+    }
+}
+
+}  // namespace hjlo

@@ -1,0 +1,65 @@
+// hjlo_internal.h -- host-side structures shared by the translation units of
+// the hjlo library (not part of the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "hjlo.h"
+#include "hjlo_device.cuh"
+
+namespace hjlo {
+
+// Resolved geometry, tables and launch shape of one axis of a grid.
+struct AxisPlan {
+    long long N = 1, inner = 1, outer = 1;
+    long long dlo = 0, dhi = 0, centre = 0;
+    int weff = 1, hoff = 0;
+    double kmin = 0, kmax = 0, curv = 0;
+    double *d_kr64 = nullptr;   // device, reversed table
+    int algo = KALGO_MONGE;
+    int layout = LAYOUT_CONTIG;
+    int C = 1, log2C = 0, wpl = 1, threads = 32;
+    int lpl = 32, log2lpl = 5, seg = 1;   // MONGE: lanes per line, odd segment
+    int gs = 1, tp = 2;                    // MONGE pivot group; argmin row pitch
+    int by = 1, nbox = 1, lp = 0;
+    long long ntiles = 0, tiles_per_outer = 1;
+    size_t smem = 0;
+    int off_u = 0, off_fx = 0, off_kfx = 0, off_t = 0, off_k64 = 0, off_misc = 0;
+};
+
+// Records an error for hjlo_last_error() and returns it.
+hjlo_status set_error(hjlo_status st, const char *fmt, ...);
+hjlo_status cuda_error(cudaError_t e, const char *what);
+
+// Host kernel tables of eq. cost2 for one axis (binary64, fixed order).
+double kernel_entry(long long d, double dx, double h, double P);
+hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W, AxisPlan &ax,
+                         double **kr64_host);
+
+// Chooses lines per tile, warps per line and shared-memory layout.
+hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin);
+
+// Enqueues one pass. src/dst may alias.  hv may be null.  amin may be null.
+// hv_scale != 0: hv holds V and the potential term is fl(m - fl(hv_scale*V)).
+hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *dst, const double *hv,
+                        double hv_scale, int32_t *amin, unsigned long long *counters, int *flags,
+                        cudaStream_t st);
+
+// One-time per-device kernel attributes; call outside stream capture.
+hjlo_status prepare_kernels();
+
+const char *last_error_cstr();
+void clear_error();
+
+// Device properties used for launch shaping.
+struct DeviceFacts {
+    int device = 0, num_sms = 0;
+    size_t smem_optin = 0;
+};
+hjlo_status device_facts(DeviceFacts &f);
+
+}  // namespace hjlo

@@ -1,0 +1,239 @@
+"""Python binding of the hjlo C ABI (include/hjlo.h): argument marshalling only.
+
+Every step of the scheme runs in the library's sm_103a kernels; this module
+checks tensors, passes raw device pointers and the torch stream handle, and
+turns status codes into exceptions.  There is no CPU fallback: if the
+compiled library cannot be loaded, importing it raises.
+
+    plan = Plan(shape=(1024, 1024), dx=1/1024, h=0.02, P=(0.3, 0.1), W=64)
+    plan.run(u, V, nsteps=1000)          # u: cuda float64 tensor, in place
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Plan", "HjloError", "lib", "library_path", "exported_symbols",
+           "F64", "F32_STORAGE", "ALGO_AUTO", "ALGO_BRUTE", "ALGO_MONGE"]
+
+F64, F32_STORAGE = 0, 1
+ALGO_AUTO, ALGO_BRUTE, ALGO_MONGE = 0, 1, 2
+_STATUS = {0: "HJLO_OK", 1: "HJLO_EINVAL", 2: "HJLO_ENOMEM", 3: "HJLO_ECUDA", 4: "HJLO_EPRECOND",
+           5: "HJLO_ETIMEOUT", 6: "HJLO_EUNSUPPORTED"}
+
+_i32, _i64, _f64, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("ndim", _i32), ("dtype", _i32), ("algo", _i32), ("reserved", _i32),
+                ("shape", _i64 * 3), ("dx", _f64 * 3), ("h", _f64), ("P", _f64 * 3),
+                ("window", _i64 * 3)]
+
+
+class Facts(ctypes.Structure):
+    _fields_ = [("ndim", _i32), ("algo", _i32), ("dlo", _i64 * 3), ("dhi", _i64 * 3),
+                ("centre", _i64 * 3), ("kmin", _f64 * 3), ("curvature", _f64 * 3), ("npts", _i64)]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("exact_rescans", _i64), ("brute_fallback_lines", _i64), ("steps", _i64),
+                ("error_flags", _i32), ("reserved", _i32)]
+
+
+class HjloError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+        super().__init__("%s failed: %s (%s)" % (where, self.name, msg))
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/hjlo.h
+_SIGS = [
+    ("hjlo_version", _i32, []),
+    ("hjlo_last_error", ctypes.c_char_p, []),
+    ("hjlo_plan_create", _i32, [ctypes.POINTER(Desc), _vp, ctypes.POINTER(_vp)]),
+    ("hjlo_plan_destroy", _i32, [_vp]),
+    ("hjlo_plan_info", _i32, [_vp, ctypes.POINTER(Facts)]),
+    ("hjlo_step", _i32, [_vp, _vp, _vp, _vp, _vp]),
+    ("hjlo_run", _i32, [_vp, _vp, _vp, _i64]),
+    ("hjlo_run_tv", _i32, [_vp, _vp, _vp, _i64]),
+    ("hjlo_run_host", _i32, [_vp, _vp, _vp, _i64]),
+    ("hjlo_hbar", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(_f64)]),
+    ("hjlo_sync", _i32, [_vp, ctypes.POINTER(Counters)]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def exported_symbols() -> list[str]:
+    return [s[0] for s in _SIGS]
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) the compiled library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, res, args in _SIGS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        msg = lib().hjlo_last_error()
+        raise HjloError(st, where, msg.decode() if msg else "")
+
+
+def _per_axis(x, nd, typ):
+    a = list(np.atleast_1d(np.asarray(x, dtype=typ)).tolist())
+    if len(a) == 1 and nd > 1:
+        a = a * nd
+    if len(a) != nd:
+        raise ValueError("expected %d per-axis values" % nd)
+    return a + [typ(0)] * (3 - nd)
+
+
+def make_desc(shape, dx, h, P, W, dtype=F64, algo=ALGO_AUTO) -> Desc:
+    shape = tuple(int(s) for s in np.atleast_1d(shape))
+    nd = len(shape)
+    d = Desc()
+    d.ndim = nd
+    d.dtype = int(dtype)
+    d.algo = int(algo)
+    d.reserved = 0
+    d.shape[:] = list(shape) + [1] * (3 - nd)
+    d.dx[:] = _per_axis(dx, nd, float)
+    d.h = float(h)
+    d.P[:] = _per_axis(P, nd, float)
+    d.window[:] = _per_axis(W, nd, int)
+    return d
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """One grid of the scheme (see hjlo_plan_create).  Tensors are torch CUDA
+    tensors of the plan's storage dtype (float64, or float32 for F32_STORAGE);
+    V is float64."""
+
+    def __init__(self, shape, dx, h, P, W=0, dtype=F64, algo=ALGO_AUTO, stream=None):
+        import torch
+        self.shape = tuple(int(s) for s in np.atleast_1d(shape))
+        self.ndim = len(self.shape)
+        self.npts = int(np.prod(self.shape))
+        self.h = float(h)
+        self.dtype_code = int(dtype)
+        self.torch_dtype = torch.float64 if dtype == F64 else torch.float32
+        self._desc = make_desc(shape, dx, h, P, W, dtype, algo)
+        self._stream = _stream_handle(stream)
+        handle = _vp()
+        _check(lib().hjlo_plan_create(ctypes.byref(self._desc), _vp(self._stream), ctypes.byref(handle)),
+               "hjlo_plan_create")
+        self._h = handle
+
+    # -- helpers
+    def _u(self, t, name):
+        if not t.is_cuda or t.dtype != self.torch_dtype or t.numel() != self.npts or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA %s tensor with %d elements"
+                             % (name, self.torch_dtype, self.npts))
+        return _vp(t.data_ptr())
+
+    def _v(self, V, count=1):
+        import torch
+        if V is None:
+            return None
+        if not V.is_cuda or V.dtype != torch.float64 or V.numel() != count * self.npts or not V.is_contiguous():
+            raise ValueError("V must be a contiguous CUDA float64 tensor with %d elements" % (count * self.npts))
+        return _vp(V.data_ptr())
+
+    # -- API
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hjlo_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        f = Facts()
+        _check(lib().hjlo_plan_info(self._h, ctypes.byref(f)), "hjlo_plan_info")
+        nd = f.ndim
+        return {"algo": {1: "brute", 2: "monge"}.get(f.algo, f.algo), "npts": f.npts,
+                "dlo": list(f.dlo[:nd]), "dhi": list(f.dhi[:nd]), "centre": list(f.centre[:nd]),
+                "kmin": list(f.kmin[:nd]), "curvature": list(f.curvature[:nd])}
+
+    def step(self, u_in, u_out=None, V=None, argmin=None):
+        """One step; returns u_out (u_in itself when u_out is None: in place)."""
+        import torch
+        if u_out is None:
+            u_out = u_in
+        am = None
+        if argmin is not None:
+            if argmin.dtype != torch.int32 or argmin.numel() != self.ndim * self.npts or not argmin.is_cuda \
+                    or not argmin.is_contiguous():
+                raise ValueError("argmin must be a contiguous CUDA int32 tensor of ndim*npts elements")
+            am = _vp(argmin.data_ptr())
+        _check(lib().hjlo_step(self._h, self._u(u_in, "u_in"), self._u(u_out, "u_out"), self._v(V), am),
+               "hjlo_step")
+        return u_out
+
+    def run(self, u, V=None, nsteps=1):
+        _check(lib().hjlo_run(self._h, self._u(u, "u"), self._v(V), int(nsteps)), "hjlo_run")
+        return u
+
+    def run_tv(self, u, V, nsteps):
+        _check(lib().hjlo_run_tv(self._h, self._u(u, "u"), self._v(V, int(nsteps)), int(nsteps)), "hjlo_run_tv")
+        return u
+
+    def run_host(self, u: np.ndarray, V: np.ndarray | None, nsteps: int):
+        """End to end from host arrays (in place on u)."""
+        want = np.float64 if self.dtype_code == F64 else np.float32
+        if u.dtype != want or u.size != self.npts or not u.flags.c_contiguous:
+            raise ValueError("u must be a C-contiguous %s array of %d elements" % (want, self.npts))
+        vp = None
+        if V is not None:
+            if V.dtype != np.float64 or V.size != self.npts or not V.flags.c_contiguous:
+                raise ValueError("V must be a C-contiguous float64 array")
+            vp = _vp(V.ctypes.data)
+        _check(lib().hjlo_run_host(self._h, _vp(u.ctypes.data), vp, int(nsteps)), "hjlo_run_host")
+        return u
+
+    def hbar(self, u0, un, nsteps):
+        out = (_f64 * 3)()
+        _check(lib().hjlo_hbar(self._h, self._u(u0, "u0"), self._u(un, "un"), int(nsteps), out), "hjlo_hbar")
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def sync(self) -> dict:
+        c = Counters()
+        st = lib().hjlo_sync(self._h, ctypes.byref(c))
+        res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
+               "steps": c.steps, "error_flags": c.error_flags}
+        _check(st, "hjlo_sync")
+        return res

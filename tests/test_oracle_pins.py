@@ -477,3 +477,27 @@ def test_tie_conventions_dyadic():
         assert O.window(N, dx, h, 0.25, 0) == (1 - N // 2 + 1, 1 + N // 2)
     # odd N has no antipodal tie: the window is symmetric about the minimiser
     assert O.window(9, dx, h, 0.25, 0) == (1 - 4, 1 + 4)
+
+
+@pytest.mark.parametrize("shape", [(6, 5), (4, 3, 5)])
+def test_sampled_step_equals_full_minimum_dyadic(shape):
+    """The point-wise evaluation (used to check large grids by sampling) is the
+    same n-D minimum of Remark rk28, checked by brute force on exact data."""
+    dx, h, P, W, u0, V = dyadic_problem(shape, 13, W=tuple(1 for _ in shape))
+    costs = _product_cost(shape, dx, h, P, W)
+    pts = np.arange(u0.size)
+    got = O.step_points(u0, dx, h, P, W, V, pts)
+    for q, x in enumerate(itertools.product(*[range(n) for n in shape])):
+        best = None
+        for y in itertools.product(*[range(n) for n in shape]):
+            c = Fraction(u0[y])
+            ok = True
+            for a in range(len(shape)):
+                r = (x[a] - y[a]) % shape[a]
+                if r not in costs[a]:
+                    ok = False
+                    break
+                c += costs[a][r]
+            if ok and (best is None or c < best):
+                best = c
+        assert Fraction(got[q]) == best - Fraction(h) * Fraction(V[x])
