@@ -175,6 +175,34 @@ hjlo_status hjlo_hbar(hjlo_plan *plan, const void *u0, const void *un, int64_t n
  * last call raised the corresponding flag (the flags are then cleared). */
 hjlo_status hjlo_sync(hjlo_plan *plan, hjlo_counters *out);
 
+/* Largest window (displacements per axis, after resolving W) served by
+ * hjlo_step_noalloc. */
+#define HJLO_NOALLOC_MAX_WINDOW 8192
+
+/*
+ * One time step, as hjlo_step with argmin_out = NULL, without a plan and
+ * without allocating anything -- for callers that cannot allocate device
+ * memory (a framework whose caching allocator must own all device memory,
+ * code running while another thread captures a CUDA graph, latency-bound
+ * loops that cannot afford an allocation's implicit synchronisation).  The
+ * paper has no counterpart: this is a deployment variant of the same step.
+ *   desc: the grid (host); every window must resolve to at most
+ *         HJLO_NOALLOC_MAX_WINDOW displacements, else HJLO_EUNSUPPORTED.
+ *   cuda_stream: cudaStream_t (may be NULL); all work is enqueued on it.
+ *   u_in, u_out: npts values of desc->dtype (device), equal or disjoint.
+ *   V: npts binary64 (device) or NULL; h*V is formed inside the kernel.
+ * Scratch: the kernel tables and device counters live in one static device
+ * array of the library (about 200 KB per GPU that loads it, held until the
+ * process exits); every call overwrites it and clears the counters, so calls
+ * whose GPU work overlaps (other streams, other threads) race.  The first
+ * call on a device looks up the array's device address and sets kernel
+ * attributes; make that first call before any stream capture.  The kernel
+ * tables are copied from host (pageable) memory, which orders the copy after
+ * earlier work on the stream.  Results equal hjlo_step's bit for bit.
+ */
+hjlo_status hjlo_step_noalloc(const hjlo_desc *desc, void *cuda_stream, const void *u_in, void *u_out,
+                              const double *V);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char *hjlo_last_error(void);
 

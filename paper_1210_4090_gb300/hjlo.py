@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Plan", "HjloError", "lib", "library_path", "exported_symbols",
+__all__ = ["Plan", "HjloError", "lib", "library_path", "exported_symbols", "step_noalloc",
            "F64", "F32_STORAGE", "ALGO_AUTO", "ALGO_BRUTE", "ALGO_MONGE"]
 
 F64, F32_STORAGE = 0, 1
@@ -68,6 +68,7 @@ _SIGS = [
     ("hjlo_run_host", _i32, [_vp, _vp, _vp, _i64]),
     ("hjlo_hbar", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(_f64)]),
     ("hjlo_sync", _i32, [_vp, ctypes.POINTER(Counters)]),
+    ("hjlo_step_noalloc", _i32, [ctypes.POINTER(Desc), _vp, _vp, _vp, _vp]),
 ]
 
 
@@ -132,6 +133,26 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def step_noalloc(u_in, u_out, V, shape, dx, h, P, W=0, dtype=F64, algo=ALGO_AUTO, stream=None):
+    """One step through hjlo_step_noalloc (no plan, no allocation): the kernel
+    tables live in the library's static device scratch array."""
+    import torch
+    desc = make_desc(shape, dx, h, P, W, dtype, algo)
+    npts = int(np.prod(np.atleast_1d(shape)))
+    want = torch.float64 if dtype == F64 else torch.float32
+    for t, name in ((u_in, "u_in"), (u_out, "u_out")):
+        if not t.is_cuda or t.dtype != want or t.numel() != npts or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA %s tensor with %d elements" % (name, want, npts))
+    vp = None
+    if V is not None:
+        if not V.is_cuda or V.dtype != torch.float64 or V.numel() != npts or not V.is_contiguous():
+            raise ValueError("V must be a contiguous CUDA float64 tensor with %d elements" % npts)
+        vp = _vp(V.data_ptr())
+    _check(lib().hjlo_step_noalloc(ctypes.byref(desc), _vp(_stream_handle(stream)), _vp(u_in.data_ptr()),
+                                   _vp(u_out.data_ptr()), vp), "hjlo_step_noalloc")
+    return u_out
 
 
 class Plan:
