@@ -56,7 +56,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256"], default="grid1024")
+    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512"], default="grid1024")
+    ap.add_argument("--loop-instances", type=int, default=28,
+                    help="sweep512: instances timed one plan at a time for the per-instance loop")
     ap.add_argument("--algo", choices=["monge", "brute", "auto"], default="monge")
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-oracle sample budget")
@@ -210,6 +212,152 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """sweep512: all instances in one batch (grouped launches, one CUDA graph)
+    against the plain per-instance loop (one plan and hjlo_run per instance)."""
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1210_4090_gb300 import hjlo
+
+    # instances are independent: rank r takes every world-th instance
+    allp = WL.sweep512()
+    probs = allp[rank::world]
+    nsteps = probs[0].nsteps
+    dev = torch.device("cuda", local)
+    sizes = [p.npts for p in probs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    u0_all = torch.tensor(np.concatenate([p.u0.ravel() for p in probs]), device=dev)
+    V_all = torch.tensor(np.concatenate([p.V.ravel() for p in probs]), device=dev)
+    u_all = torch.empty_like(u0_all)
+    us = [u_all[offs[i]:offs[i + 1]] for i in range(len(probs))]
+    u0s = [u0_all[offs[i]:offs[i + 1]] for i in range(len(probs))]
+    Vs = [V_all[offs[i]:offs[i + 1]] for i in range(len(probs))]
+    algo = {"monge": hjlo.ALGO_MONGE, "brute": hjlo.ALGO_BRUTE, "auto": hjlo.ALGO_AUTO}[args.algo]
+    batch = hjlo.Batch([(p.shape, p.dx, p.h, p.P, p.W) for p in probs], algo=algo)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        u_all.copy_(u0_all)
+        batch.run(us, Vs, nsteps)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_uuid = None
+    clocks = ClockSampler(gpu_uuid)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    for _ in range(args.steps):
+        u_all.copy_(u0_all)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run(us, Vs, nsteps)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    updates_local = int(sum(sizes)) * nsteps
+    if world > 1:
+        t = torch.tensor([total_ms, updates_local], dtype=torch.float64, device=dev)
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tu = t[1:].clone()
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        total_ms, updates = float(tm.item()), int(tu.item())
+    else:
+        updates = updates_local
+    ms_per_step = total_ms / args.steps
+    value = updates * args.steps / (total_ms * 1e-3)
+    hb = batch.hbar(u0s, us, nsteps)
+    cnt = batch.sync()
+    groups = batch.groups()
+
+    # plain per-instance loop on a subset with the same size mix
+    loop = None
+    if rank == 0 and args.loop_instances > 0:
+        sub = probs[:args.loop_instances]
+        plans = [hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W, algo=algo) for p in sub]
+        for pl, i in zip(plans, range(len(sub))):
+            us[i].copy_(u0s[i])
+            pl.run(us[i], Vs[i], 2 * 16)          # warm: capture each plan's graph
+        torch.cuda.synchronize()
+        for i in range(len(sub)):
+            us[i].copy_(u0s[i])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for pl, i in zip(plans, range(len(sub))):
+            pl.run(us[i], Vs[i], nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lms = e0.elapsed_time(e1)
+        lupd = sum(p.npts for p in sub) * nsteps
+        loop = {"value": lupd / (lms * 1e-3), "unit": UNIT, "instances": len(sub), "ms": lms}
+        for pl in plans:
+            pl.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        cores = O.max_threads()
+        t0 = time.perf_counter()
+        n_done = 0
+        k = 0
+        while time.perf_counter() - t0 < args.cpu_seconds and k < len(probs):
+            p = probs[k]
+            O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, 50)
+            n_done += p.npts * 50
+            k += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": n_done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "sweep512 instances 0..%d, first 50 of %d steps each, %d OpenMP threads"
+                         % (k - 1, nsteps, cores)}
+
+    launches = nsteps * 2 * groups
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    alg_bytes_run = updates_local * 40.0            # 2D binary64: 2 passes x 16 B + h*V 8 B
+    avg_launch_s = ms_per_step * 1e-3 / launches
+    achieved = alg_bytes_run / launches / avg_launch_s / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "sweep512", "instances": len(allp), "nsteps": nsteps,
+                           "sizes": sorted(set(p.shape[0] for p in allp)), "h": 0.02, "W": "N/16",
+                           "launch_groups": groups, "updates_per_step": updates,
+                           "l2": "256 MiB buffer written between timed steps",
+                           "parallelism": "instances sharded over ranks" if world > 1 else "single GPU"},
+                "per_instance_loop": loop,
+                "batched_vs_loop": (value / world / loop["value"]) if loop else None,
+                "hbar": {"mean": float(hb[:, 0].mean()), "min": float(hb[:, 0].min()),
+                         "max": float(hb[:, 0].max()), "first": [float(x) for x in hb[:4, 0]]},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "traffic": None,
+                             "kernel": "hjlo::pass_kernel_batch", "peak_kind": peak_kind,
+                             "alg_bytes_per_launch": alg_bytes_run / launches,
+                             "avg_launch_us": avg_launch_s * 1e6},
+                "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(args.steps * (len(probs) + launches)), "counters": cnt}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -339,6 +487,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep512":
+        run_sweep(args)
     else:
         run_ours(args)
 

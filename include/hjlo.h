@@ -170,6 +170,41 @@ hjlo_status hjlo_run_host(hjlo_plan *plan, void *u_host, const double *V_host, i
 hjlo_status hjlo_hbar(hjlo_plan *plan, const void *u0, const void *un, int64_t nsteps,
                       double *out3);
 
+/*
+ * Batched grids: `count` independent instances of the scheme (each its own
+ * descriptor: P, grid size, window, h) advanced together -- the sweep of the
+ * discrete effective Hamiltonian over P of Prop. prop:klm.  Instances with
+ * the same shape and window sizes share kernel launches (the convolution
+ * blocks are independent, Sec. 4.1), and the groups run as parallel branches
+ * of one captured CUDA graph.  Every instance's result is identical, bit for
+ * bit, to a single plan's.  All descriptors must share ndim and dtype.
+ * Errors as hjlo_plan_create (the message names the instance).
+ */
+typedef struct hjlo_batch hjlo_batch;
+hjlo_status hjlo_batch_create(const hjlo_desc *descs, int32_t count, void *cuda_stream, hjlo_batch **out);
+
+/* Release a batch (synchronises its stream first).  NULL is accepted. */
+hjlo_status hjlo_batch_destroy(hjlo_batch *batch);
+
+/*
+ * nsteps time steps of every instance, in place.  u: host array of `count`
+ * device pointers (instance i: npts_i values of the dtype).  V: NULL, or a
+ * host array of `count` device pointers to time-independent binary64
+ * potentials (an entry may be NULL for V = 0).
+ */
+hjlo_status hjlo_batch_run(hjlo_batch *batch, void *const *u, const double *const *V, int64_t nsteps);
+
+/* hjlo_hbar for every instance: out3 (host) receives 3*count doubles,
+ * {estimate, lower, upper} per instance.  Synchronises the batch's stream. */
+hjlo_status hjlo_batch_hbar(hjlo_batch *batch, const void *const *u0, const void *const *un, int64_t nsteps,
+                            double *out3);
+
+/* hjlo_sync for a batch. */
+hjlo_status hjlo_batch_sync(hjlo_batch *batch, hjlo_counters *out);
+
+/* Number of launch groups the batch formed (0 for NULL). */
+int32_t hjlo_batch_groups(const hjlo_batch *batch);
+
 /* Wait for the plan's stream and copy its device counters into *out (host,
  * may be NULL).  Returns HJLO_EPRECOND / HJLO_ETIMEOUT if a launch since the
  * last call raised the corresponding flag (the flags are then cleared). */

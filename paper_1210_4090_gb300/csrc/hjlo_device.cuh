@@ -370,8 +370,10 @@ struct LineInfo {
     int pad;
 };
 
+// One tile of one axis pass (everything a CTA does).  `tmap` is the 3D TMA
+// descriptor of the source for strided lines (unused otherwise).
 template <typename T, int LAYOUT, int ALGO>
-__global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUtensorMap tmap, PassParams p)
+__device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassParams &p, long long tile)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     T *su = reinterpret_cast<T *>(smem + p.off_u);
@@ -385,8 +387,6 @@ __global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUte
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int N = (int)p.N, C = p.C, weff = p.weff;
-    const long long tile = blockIdx.x;
-    if (tile >= p.ntiles) return;
     const Tile<LAYOUT> tl = tile_of<LAYOUT>(p, tile);
     const T *src = reinterpret_cast<const T *>(p.src);
 
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUte
                 long long o = tile / p.tiles_per_outer;
                 int x0 = (int)((tile - o * p.tiles_per_outer) << p.log2C);
                 for (int b = 0; b < p.nbox; ++b)
-                    tma_tensor_load_3d(su + (long long)b * p.by * C, &tmap, x0, b * p.by, (int)o, bar);
+                    tma_tensor_load_3d(su + (long long)b * p.by * C, tmap, x0, b * p.by, (int)o, bar);
             }
         }
     } else {
@@ -699,6 +699,52 @@ __global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUte
         if (scnt[0]) atomicAdd(&p.counters[CNT_RESCAN], (unsigned long long)scnt[0]);
         if (scnt[1]) atomicAdd(&p.counters[CNT_FALLBACK], (unsigned long long)scnt[1]);
     }
+}
+
+template <typename T, int LAYOUT, int ALGO>
+__global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUtensorMap tmap, PassParams p)
+{
+    const long long tile = blockIdx.x;
+    if (tile >= p.ntiles) return;
+    pass_tile<T, LAYOUT, ALGO>(&tmap, p, tile);
+}
+
+// Per-instance fields of a batched pass: one entry per grid of the batch.
+struct BatchItem {
+    CUtensorMap tmap;          // 3D TMA descriptor of this instance's u (strided lines)
+    const void *src;
+    void *dst;
+    const double *hv;          // this instance's h*V (last axis) or nullptr
+    const double *kr64;        // this instance's reversed kernel table
+    double kmax, curv;
+    int hoff, dhi;
+    int use_tma, pad;
+};
+
+// One axis pass over many grids of the same launch shape: block b handles
+// tile (b mod tiles) of instance (b / tiles).  Fields that differ between
+// instances come from `items`; the rest of `p` is shared.
+template <typename T, int LAYOUT, int ALGO>
+__global__ void __launch_bounds__(1024) pass_kernel_batch(const BatchItem *__restrict__ items, PassParams p,
+                                                          long long count)
+{
+    const long long inst = blockIdx.x / p.ntiles;
+    const long long tile = blockIdx.x - inst * p.ntiles;
+    if (inst >= count) return;
+    const BatchItem *it = items + inst;
+    PassParams q = p;
+    q.src = it->src;
+    q.dst = it->dst;
+    q.hv = it->hv;
+    q.kr64 = it->kr64;
+    q.kmax = it->kmax;
+    q.curv = it->curv;
+    q.hoff = it->hoff;
+    q.dhi = it->dhi;
+    q.use_tma = it->use_tma;
+    if (q.use_tma && LAYOUT == LAYOUT_STRIDED && threadIdx.x == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it->tmap) : "memory");
+    pass_tile<T, LAYOUT, ALGO>(&it->tmap, q, tile);
 }
 
 }  // namespace hjlo

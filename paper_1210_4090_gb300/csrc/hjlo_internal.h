@@ -40,8 +40,18 @@ double kernel_entry(long long d, double dx, double h, double P);
 hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W, AxisPlan &ax,
                          double **kr64_host);
 
-// Chooses lines per tile, warps per line and shared-memory layout.
-hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin);
+// Chooses lines per tile, lanes per line and shared-memory layout; `replicas`
+// grids of this shape run in the same launch (batched passes).
+hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
+                         long long replicas = 1);
+
+// 3D TMA descriptor {inner, N, outer} of `ptr` for lines along a strided
+// axis; false if TMA cannot serve this pointer/shape.
+bool encode_strided(const AxisPlan &ax, int esize, const void *ptr, CUtensorMap *map);
+
+// Enqueues one batched pass over `count` grids sharing ax's launch shape.
+hjlo_status launch_pass_batch(const AxisPlan &ax, int dtype, const BatchItem *d_items, long long count,
+                              unsigned long long *counters, int *flags, cudaStream_t st);
 
 // Enqueues one pass. src/dst may alias.  hv may be null.  amin may be null.
 // hv_scale != 0: hv holds V and the potential term is fl(m - fl(hv_scale*V)).

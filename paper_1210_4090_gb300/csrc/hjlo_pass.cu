@@ -185,12 +185,12 @@ static int pivot_group(int weff, int S, int lpl, double *cost)
     return best;
 }
 
-hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin)
+hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin, long long replicas)
 {
     ax.algo = algo;
     ax.layout = (ax.inner == 1) ? LAYOUT_CONTIG : LAYOUT_STRIDED;
     const long long N = ax.N;
-    const long long nlines = ax.inner * ax.outer;
+    const long long nlines = ax.inner * ax.outer * std::max(1LL, replicas);
     ax.tp = (int)N;
     while (ax.tp % 4 != 2) ++ax.tp;
     if (ax.layout == LAYOUT_STRIDED) {
@@ -265,7 +265,8 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
     if (ax.smem > smem_optin || (long long)C * lanes > 1024)
         return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit in shared memory", N);
     const size_t budget = 110 * 1024;
-    while (2 * C <= std::max(cmax, C) && (long long)2 * C * lanes <= 512 && tiles_for(2 * C) >= 2LL * num_sms) {
+    while (2 * C <= std::max(cmax, C) && (long long)2 * C * lanes <= 512 &&
+           tiles_for(2 * C) * std::max(1LL, replicas) >= 2LL * num_sms) {
         AxisPlan t = ax;
         t.C = 2 * C;
         layout_smem(t, esize, algo);
@@ -300,7 +301,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 // 3D view {inner, N, outer} of the grid for lines along a strided axis; box
 // {C, by, 1}.  Returns false if TMA cannot be used for this pointer.
-static bool encode_strided(const AxisPlan &ax, int esize, const void *ptr, CUtensorMap *map)
+bool encode_strided(const AxisPlan &ax, int esize, const void *ptr, CUtensorMap *map)
 {
     if (((uintptr_t)ptr & 15) || ((ax.inner * esize) & 15) || ((ax.C * esize) & 15)) return false;
     if (ax.inner > (1LL << 32) || ax.N > (1LL << 32) || ax.outer > (1LL << 32)) return false;
@@ -324,6 +325,9 @@ static hjlo_status allow_smem()
 {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<T, LAYOUT, ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pass_kernel_batch<T, LAYOUT, ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024);
     return e == cudaSuccess ? HJLO_OK : cuda_error(e, "cudaFuncSetAttribute");
 }
 
@@ -361,20 +365,10 @@ static hjlo_status launch_t(const AxisPlan &ax, const CUtensorMap &map, const Pa
     return HJLO_OK;
 }
 
-hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *dst, const double *hv,
-                        double hv_scale, int32_t *amin, unsigned long long *counters, int *flags,
-                        cudaStream_t st)
+static void fill_params(const AxisPlan &ax, PassParams &p)
 {
-    const int esize = (dtype == HJLO_F64) ? 8 : 4;
-    PassParams p;
     memset(&p, 0, sizeof(p));
-    p.src = src;
-    p.dst = dst;
-    p.hv = hv;
-    p.amin = amin;
     p.kr64 = ax.d_kr64;
-    p.counters = counters;
-    p.flags = flags;
     p.N = ax.N;
     p.inner = ax.inner;
     p.outer = ax.outer;
@@ -403,6 +397,21 @@ hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *ds
     p.off_k64 = ax.off_k64;
     p.off_misc = ax.off_misc;
     p.wait_ns = 500000000LL;   // 0.5 s: a tile copy takes microseconds
+}
+
+hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *dst, const double *hv,
+                        double hv_scale, int32_t *amin, unsigned long long *counters, int *flags,
+                        cudaStream_t st)
+{
+    const int esize = (dtype == HJLO_F64) ? 8 : 4;
+    PassParams p;
+    fill_params(ax, p);
+    p.src = src;
+    p.dst = dst;
+    p.hv = hv;
+    p.amin = amin;
+    p.counters = counters;
+    p.flags = flags;
     p.hscale = hv_scale;
     p.hv_scaled = (hv_scale != 0.0) ? 1 : 0;
     CUtensorMap map;
@@ -425,6 +434,40 @@ hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *ds
                               : launch_t<float, LAYOUT_STRIDED, KALGO_BRUTE>(ax, map, p, st);
     return monge ? launch_t<float, LAYOUT_CONTIG, KALGO_MONGE>(ax, map, p, st)
                  : launch_t<float, LAYOUT_CONTIG, KALGO_BRUTE>(ax, map, p, st);
+}
+
+template <typename T, int LAYOUT, int ALGO>
+static hjlo_status launch_b(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
+                            cudaStream_t st)
+{
+    long long blocks = ax.ntiles * count;
+    if (blocks > 0x7fffffffLL) return set_error(HJLO_EUNSUPPORTED, "batched launch too large");
+    pass_kernel_batch<T, LAYOUT, ALGO><<<(unsigned)blocks, ax.threads, ax.smem, st>>>(items, p, count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "batched pass kernel launch");
+    return HJLO_OK;
+}
+
+hjlo_status launch_pass_batch(const AxisPlan &ax, int dtype, const BatchItem *d_items, long long count,
+                              unsigned long long *counters, int *flags, cudaStream_t st)
+{
+    PassParams p;
+    fill_params(ax, p);
+    p.counters = counters;
+    p.flags = flags;
+    const bool f64 = (dtype == HJLO_F64);
+    const bool strided = (ax.layout == LAYOUT_STRIDED);
+    const bool monge = (ax.algo == KALGO_MONGE);
+    if (f64) {
+        if (strided) return monge ? launch_b<double, LAYOUT_STRIDED, KALGO_MONGE>(ax, d_items, p, count, st)
+                                  : launch_b<double, LAYOUT_STRIDED, KALGO_BRUTE>(ax, d_items, p, count, st);
+        return monge ? launch_b<double, LAYOUT_CONTIG, KALGO_MONGE>(ax, d_items, p, count, st)
+                     : launch_b<double, LAYOUT_CONTIG, KALGO_BRUTE>(ax, d_items, p, count, st);
+    }
+    if (strided) return monge ? launch_b<float, LAYOUT_STRIDED, KALGO_MONGE>(ax, d_items, p, count, st)
+                              : launch_b<float, LAYOUT_STRIDED, KALGO_BRUTE>(ax, d_items, p, count, st);
+    return monge ? launch_b<float, LAYOUT_CONTIG, KALGO_MONGE>(ax, d_items, p, count, st)
+                 : launch_b<float, LAYOUT_CONTIG, KALGO_BRUTE>(ax, d_items, p, count, st);
 }
 
 hjlo_status device_facts(DeviceFacts &f)

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Plan", "HjloError", "lib", "library_path", "exported_symbols", "step_noalloc",
+__all__ = ["Plan", "Batch", "HjloError", "lib", "library_path", "exported_symbols", "step_noalloc",
            "F64", "F32_STORAGE", "ALGO_AUTO", "ALGO_BRUTE", "ALGO_MONGE"]
 
 F64, F32_STORAGE = 0, 1
@@ -69,6 +69,12 @@ _SIGS = [
     ("hjlo_hbar", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(_f64)]),
     ("hjlo_sync", _i32, [_vp, ctypes.POINTER(Counters)]),
     ("hjlo_step_noalloc", _i32, [ctypes.POINTER(Desc), _vp, _vp, _vp, _vp]),
+    ("hjlo_batch_create", _i32, [ctypes.POINTER(Desc), _i32, _vp, ctypes.POINTER(_vp)]),
+    ("hjlo_batch_destroy", _i32, [_vp]),
+    ("hjlo_batch_run", _i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64]),
+    ("hjlo_batch_hbar", _i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, ctypes.POINTER(_f64)]),
+    ("hjlo_batch_sync", _i32, [_vp, ctypes.POINTER(Counters)]),
+    ("hjlo_batch_groups", _i32, [_vp]),
 ]
 
 
@@ -257,4 +263,72 @@ class Plan:
         res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
                "steps": c.steps, "error_flags": c.error_flags}
         _check(st, "hjlo_sync")
+        return res
+
+
+class Batch:
+    """Many independent grids advanced together (hjlo_batch_*).  `problems` is a
+    list of (shape, dx, h, P, W) tuples; tensors are passed as lists."""
+
+    def __init__(self, problems, dtype=F64, algo=ALGO_AUTO, stream=None):
+        import torch
+        self.count = len(problems)
+        descs = (Desc * self.count)()
+        self.npts = []
+        for i, (shape, dx, h, P, W) in enumerate(problems):
+            descs[i] = make_desc(shape, dx, h, P, W, dtype, algo)
+            self.npts.append(int(np.prod(np.atleast_1d(shape))))
+        self._descs = descs
+        self.torch_dtype = torch.float64 if dtype == F64 else torch.float32
+        self._stream = _stream_handle(stream)
+        handle = _vp()
+        _check(lib().hjlo_batch_create(descs, self.count, _vp(self._stream), ctypes.byref(handle)),
+               "hjlo_batch_create")
+        self._h = handle
+
+    def _ptrs(self, ts, dtype, name, allow_none=False):
+        arr = (_vp * self.count)()
+        for i, t in enumerate(ts):
+            if t is None and allow_none:
+                arr[i] = None
+                continue
+            if not t.is_cuda or t.dtype != dtype or t.numel() != self.npts[i] or not t.is_contiguous():
+                raise ValueError("%s[%d] must be a contiguous CUDA %s tensor with %d elements"
+                                 % (name, i, dtype, self.npts[i]))
+            arr[i] = t.data_ptr()
+        return arr
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hjlo_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def groups(self) -> int:
+        return int(lib().hjlo_batch_groups(self._h))
+
+    def run(self, us, Vs=None, nsteps=1):
+        import torch
+        up = self._ptrs(us, self.torch_dtype, "u")
+        vp = None if Vs is None else self._ptrs(Vs, torch.float64, "V", allow_none=True)
+        _check(lib().hjlo_batch_run(self._h, up, vp, int(nsteps)), "hjlo_batch_run")
+        return us
+
+    def hbar(self, u0s, uns, nsteps):
+        out = (_f64 * (3 * self.count))()
+        _check(lib().hjlo_batch_hbar(self._h, self._ptrs(u0s, self.torch_dtype, "u0"),
+                                     self._ptrs(uns, self.torch_dtype, "un"), int(nsteps), out), "hjlo_batch_hbar")
+        return np.array(out[:]).reshape(self.count, 3)
+
+    def sync(self) -> dict:
+        c = Counters()
+        st = lib().hjlo_batch_sync(self._h, ctypes.byref(c))
+        res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
+               "steps": c.steps, "error_flags": c.error_flags}
+        _check(st, "hjlo_batch_sync")
         return res
