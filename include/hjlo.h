@@ -171,6 +171,35 @@ hjlo_status hjlo_hbar(hjlo_plan *plan, const void *u0, const void *un, int64_t n
                       double *out3);
 
 /*
+ * Reverse mode of nsteps steps of a binary64 plan with time-independent V:
+ * the gradient of J = <ubar_n, u^nsteps> with respect to u^0, P and V.  Every
+ * value of a pass comes from one source along the discrete optimal path
+ * (eq. raslebol, Appendix B), so the transpose of a pass routes the
+ * cotangent back along the recorded argmins; dk/dP_a = -d*dx_a (eq. cost2);
+ * the potential term of eq. eqconvol gives dJ/dV = -h * sum_n ubar^{n+1}.
+ * Forward states are checkpointed every `checkpoint_every` steps (<= 0: one
+ * segment) and each segment is recomputed once with argmin recording.
+ *   u0, V (may be NULL), ubar_n: npts binary64 (device).
+ *   ubar_0: npts (device), receives dJ/du^0 (may not alias ubar_n).
+ *   Pbar: NULL or ndim binary64 (device), receives dJ/dP.
+ *   Vbar: NULL or npts binary64 (device), receives dJ/dV.
+ *   u_n: NULL or npts binary64 (device), receives u^nsteps.
+ * ubar_0 and Vbar are summed in the order of the definition (ascending target
+ * per source), Pbar in a fixed but different order.  Plan-owned scratch:
+ * checkpoints (ceil(nsteps/S) states), argmins (S*ndim*npts int32), one
+ * state, per-line partials.  Errors: HJLO_EUNSUPPORTED for binary32 plans.
+ */
+hjlo_status hjlo_adjoint(hjlo_plan *plan, const double *u0, const double *V, int64_t nsteps,
+                         const double *ubar_n, double *ubar_0, double *Pbar, double *Vbar,
+                         int64_t checkpoint_every, double *u_n);
+
+/* out[k] = sum_x field(x) * basis[k*npts + x] for k < nbasis (device arrays,
+ * binary64; fixed summation order): gradients of coefficients of a potential
+ * V = sum_k c_k basis_k from Vbar. */
+hjlo_status hjlo_project(hjlo_plan *plan, const double *field, const double *basis, int32_t nbasis,
+                         double *out);
+
+/*
  * Batched grids: `count` independent instances of the scheme (each its own
  * descriptor: P, grid size, window, h) advanced together -- the sweep of the
  * discrete effective Hamiltonian over P of Prop. prop:klm.  Instances with

@@ -15,34 +15,7 @@ namespace {
 
 constexpr int kGraphSteps = 16;  // steps per captured graph
 
-struct GraphCache {
-    cudaGraphExec_t exec = nullptr;
-    const void *u = nullptr;
-    const double *hv = nullptr;
-};
-
 }  // namespace
-
-struct hjlo_plan {
-    hjlo_desc desc;
-    int ndim = 1;
-    int dtype = HJLO_F64;
-    int algo = HJLO_ALGO_MONGE;
-    long long npts = 1;
-    int esize = 8;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    AxisPlan ax[HJLO_MAX_DIM];
-    unsigned long long *d_counters = nullptr;  // CNT_N
-    int *d_flags = nullptr;
-    double *d_hv = nullptr;                    // npts, h*V of the current run
-    double *d_part = nullptr;                  // readout partials
-    void *d_u_host_run = nullptr;              // hjlo_run_host staging
-    double *d_V_host_run = nullptr;
-    GraphCache graph;
-    long long steps = 0;
-    int device = 0;
-};
 
 namespace {
 
@@ -218,6 +191,20 @@ hjlo_status run_impl(hjlo_plan *p, void *u, const double *V, long long nsteps, b
 
 }  // namespace
 
+namespace hjlo {
+hjlo_status plan_enqueue_step(hjlo_plan *p, const void *src, void *dst, const double *hv, double hv_scale,
+                              int32_t *amin, cudaStream_t st)
+{
+    return enqueue_step(p, src, dst, hv, hv_scale, amin, st);
+}
+hjlo_status plan_form_hv(hjlo_plan *p, const double *V) { return form_hv(p, V); }
+hjlo_status plan_run(hjlo_plan *p, void *u, const double *V, long long nsteps)
+{
+    return run_impl(p, u, V, nsteps, false);
+}
+hjlo_status plan_set_device(const hjlo_plan *p) { return set_device(p); }
+}  // namespace hjlo
+
 extern "C" {
 
 int32_t hjlo_version(void) { return HJLO_VERSION; }
@@ -307,6 +294,11 @@ hjlo_status hjlo_plan_destroy(hjlo_plan *p)
     cudaFree(p->d_part);
     cudaFree(p->d_u_host_run);
     cudaFree(p->d_V_host_run);
+    cudaFree(p->d_ckpt);
+    cudaFree(p->d_amin);
+    cudaFree(p->d_work);
+    cudaFree(p->d_pbar_part);
+    cudaFree(p->d_proj);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
     return HJLO_OK;

@@ -72,4 +72,54 @@ struct DeviceFacts {
 };
 hjlo_status device_facts(DeviceFacts &f);
 
+// Graph of a plan's time loop, captured for one (u, h*V) pair.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    const void *u = nullptr;
+    const double *hv = nullptr;
+};
+
+}  // namespace hjlo
+
+// A plan: one grid, its tables, launch shapes and scratch.
+struct hjlo_plan {
+    hjlo_desc desc;
+    int ndim = 1;
+    int dtype = HJLO_F64;
+    int algo = HJLO_ALGO_MONGE;
+    long long npts = 1;
+    int esize = 8;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    hjlo::AxisPlan ax[HJLO_MAX_DIM];
+    unsigned long long *d_counters = nullptr;  // CNT_N
+    int *d_flags = nullptr;
+    double *d_hv = nullptr;                    // npts, h*V of the current run
+    double *d_part = nullptr;                  // readout partials
+    void *d_u_host_run = nullptr;              // hjlo_run_host staging
+    double *d_V_host_run = nullptr;
+    hjlo::GraphCache graph;
+    long long steps = 0;
+    int device = 0;
+    // adjoint scratch (allocated on first use)
+    double *d_ckpt = nullptr;                  // checkpoints, ckpt_cap states
+    long long ckpt_cap = 0;
+    int32_t *d_amin = nullptr;                 // argmins of one segment
+    long long amin_cap = 0;                    // steps of argmins held
+    double *d_work = nullptr;                  // recomputed state
+    long long work_cap = 0;
+    double *d_pbar_part = nullptr;             // per-line P partials, then one spare slot
+    long long pbar_cap = 0;
+    double *d_proj = nullptr;                  // projection partials
+    long long proj_cap = 0;
+};
+
+namespace hjlo {
+// Steps of the plan (shared with the adjoint): src -> dst for axis 0, then in
+// place; h*V precomputed (hv_scale = 0) or formed in the kernel.
+hjlo_status plan_enqueue_step(hjlo_plan *p, const void *src, void *dst, const double *hv, double hv_scale,
+                              int32_t *amin, cudaStream_t st);
+hjlo_status plan_form_hv(hjlo_plan *p, const double *V);
+hjlo_status plan_run(hjlo_plan *p, void *u, const double *V, long long nsteps);
+hjlo_status plan_set_device(const hjlo_plan *p);
 }  // namespace hjlo

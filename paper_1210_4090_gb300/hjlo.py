@@ -75,6 +75,8 @@ _SIGS = [
     ("hjlo_batch_hbar", _i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, ctypes.POINTER(_f64)]),
     ("hjlo_batch_sync", _i32, [_vp, ctypes.POINTER(Counters)]),
     ("hjlo_batch_groups", _i32, [_vp]),
+    ("hjlo_adjoint", _i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp]),
+    ("hjlo_project", _i32, [_vp, _vp, _vp, _i32, _vp]),
 ]
 
 
@@ -251,6 +253,33 @@ class Plan:
             vp = _vp(V.ctypes.data)
         _check(lib().hjlo_run_host(self._h, _vp(u.ctypes.data), vp, int(nsteps)), "hjlo_run_host")
         return u
+
+    def adjoint(self, u0, V, nsteps, ubar_n, checkpoint_every=0, want_P=True, want_V=True, want_un=False):
+        """Gradient of <ubar_n, u^nsteps> w.r.t. u0, P and V (hjlo_adjoint).
+        Returns (ubar0, Pbar, Vbar, u_n) as CUDA tensors (None where not asked)."""
+        import torch
+        if self.dtype_code != F64:
+            raise ValueError("the adjoint needs a float64 plan")
+        ubar0 = torch.empty_like(u0)
+        Pbar = torch.empty(self.ndim, dtype=torch.float64, device=u0.device) if want_P else None
+        Vbar = torch.empty_like(u0) if want_V else None
+        un = torch.empty_like(u0) if want_un else None
+        ptr = (lambda t: None if t is None else _vp(t.data_ptr()))
+        _check(lib().hjlo_adjoint(self._h, self._u(u0, "u0"), self._v(V), int(nsteps), self._u(ubar_n, "ubar_n"),
+                                  ptr(ubar0), ptr(Pbar), ptr(Vbar), int(checkpoint_every), ptr(un)), "hjlo_adjoint")
+        return ubar0, Pbar, Vbar, un
+
+    def project(self, field, basis):
+        """out[k] = sum_x field(x) basis[k](x) (hjlo_project)."""
+        import torch
+        nb = basis.shape[0]
+        if basis.dtype != torch.float64 or not basis.is_cuda or basis.numel() != nb * self.npts \
+                or not basis.is_contiguous():
+            raise ValueError("basis must be a contiguous CUDA float64 tensor (nbasis, *shape)")
+        out = torch.empty(nb, dtype=torch.float64, device=basis.device)
+        _check(lib().hjlo_project(self._h, self._v(field), _vp(basis.data_ptr()), int(nb), _vp(out.data_ptr())),
+               "hjlo_project")
+        return out
 
     def hbar(self, u0, un, nsteps):
         out = (_f64 * 3)()
