@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512"], default="grid1024")
+    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512", "adjoint512"],
+                    default="grid1024")
     ap.add_argument("--loop-instances", type=int, default=28,
                     help="sweep512: instances timed one plan at a time for the per-instance loop")
     ap.add_argument("--algo", choices=["monge", "brute", "auto"], default="monge")
@@ -358,6 +359,114 @@ def run_sweep(args):
         dist.destroy_process_group()
 
 
+def plain_adjoint_loop(p, plan, u0, V, ub_n, dev):
+    """The plain per-step reverse loop: argmins of every step kept (no
+    checkpoints), each pass transposed with torch's index_add_ (atomic
+    scatter) -- the straightforward way to differentiate the scheme."""
+    import torch
+    nd, npts, n = p.ndim, p.npts, p.nsteps
+    am = torch.empty((n, nd, npts), dtype=torch.int32, device=dev)
+    u = u0.clone()
+    for k in range(n):
+        plan.step(u, u, V, argmin=am[k].view(-1))
+    ub = ub_n.clone().view(p.shape)
+    Vbar = torch.zeros_like(u)
+    Pbar = torch.zeros(nd, dtype=torch.float64, device=dev)
+    lin = torch.arange(npts, device=dev).view(p.shape)
+    for k in range(n - 1, -1, -1):
+        Vbar -= p.h * ub
+        for a in range(nd - 1, -1, -1):
+            d = am[k, a].view(p.shape).to(torch.int64)
+            shp = [1] * nd
+            shp[a] = p.shape[a]
+            i_a = torch.arange(p.shape[a], device=dev).view(shp)
+            src = torch.remainder(i_a - d, p.shape[a])
+            Pbar[a] += (ub * (-d.to(torch.float64) * p.dx[a])).sum()
+            stride = int(np.prod(p.shape[a + 1:])) if a + 1 < nd else 1
+            srcflat = lin + (src - i_a) * stride
+            nub = torch.zeros(npts, dtype=torch.float64, device=dev)
+            nub.index_add_(0, srcflat.reshape(-1), ub.reshape(-1))
+            ub = nub.view(p.shape)
+    return ub, Pbar, Vbar
+
+
+def run_adjoint(args):
+    """adjoint512: gradient of loss = mean (u^n - u^0)/(n h) w.r.t. P and the 64
+    coefficients of V through hjlo_adjoint (checkpoint every 100 steps), against
+    the plain per-step loop."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1210_4090_gb300 import hjlo
+
+    p = WL.adjoint512()
+    dev = torch.device("cuda", local)
+    n, S = p.nsteps, p.extra["checkpoint_every"]
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W)
+    u0 = torch.tensor(p.u0, device=dev)
+    V = torch.tensor(p.V, device=dev)
+    B = torch.tensor(WL.adjoint_basis(p.shape[0]), device=dev)
+    ub_n = torch.full(p.shape, 1.0 / (p.npts * n * p.h), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        g0, gP, gV, _ = plan.adjoint(u0, V, n, ub_n, S)
+        return gP, plan.project(gV, B)
+
+    for _ in range(max(3, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_uuid = None
+    clocks = ClockSampler(gpu_uuid)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gP, gc = one()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = float(sum(a.elapsed_time(b) for a, b in evs)) / args.steps
+    updates = p.npts * n
+    gP, gc = gP.cpu().numpy(), gc.cpu().numpy()
+
+    # the plain per-step loop, timed once after a warm-up on a short run
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ub0, lP, lV = plain_adjoint_loop(p, plan, u0, V, ub_n, dev)
+    lc = plan.project(lV.contiguous(), B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1)
+    lP, lc = lP.cpu().numpy(), lc.cpu().numpy()
+    agree = {"Pbar_max_rel": float(np.max(np.abs(lP - gP) / np.maximum(np.abs(gP), 1e-300))),
+             "coef_max_rel": float(np.max(np.abs(lc - gc)) / np.max(np.abs(gc)))}
+    if rank == 0:
+        line = {"metric": METRIC + " (adjoint: forward + reverse)", "value": updates / (ms * 1e-3), "unit": UNIT,
+                "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "adjoint512", "shape": list(p.shape), "nsteps": n, "W": list(p.W),
+                           "checkpoint_every": S, "P": list(p.P), "coefficients": 64},
+                "plain_loop": {"ms": loop_ms, "value": updates / (loop_ms * 1e-3), "unit": UNIT,
+                               "how": "all argmins kept, torch index_add_ per pass"},
+                "adjoint_vs_loop": loop_ms / ms, "gradients": {"Pbar": [float(x) for x in gP],
+                                                               "coef_first": [float(x) for x in gc[:4]]},
+                "agreement_with_loop": agree, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -489,6 +598,8 @@ def main():
         run_reference(args)
     elif args.workload == "sweep512":
         run_sweep(args)
+    elif args.workload == "adjoint512":
+        run_adjoint(args)
     else:
         run_ours(args)
 
