@@ -226,8 +226,9 @@ def run_sweep(args):
     from paper_1210_4090_gb300 import hjlo
 
     # instances are independent: rank r takes every world-th instance
+    from paper_1210_4090_gb300 import dist as D
     allp = WL.sweep512()
-    probs = allp[rank::world]
+    probs = D.shard(allp, rank, world)
     nsteps = probs[0].nsteps
     dev = torch.device("cuda", local)
     sizes = [p.npts for p in probs]
@@ -271,15 +272,7 @@ def run_sweep(args):
     clk = clocks.stop()
     total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
     updates_local = int(sum(sizes)) * nsteps
-    if world > 1:
-        t = torch.tensor([total_ms, updates_local], dtype=torch.float64, device=dev)
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        tu = t[1:].clone()
-        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
-        total_ms, updates = float(tm.item()), int(tu.item())
-    else:
-        updates = updates_local
+    total_ms, updates = D.reduce_step(total_ms, updates_local, dev)
     ms_per_step = total_ms / args.steps
     value = updates * args.steps / (total_ms * 1e-3)
     hb = batch.hbar(u0s, us, nsteps)
@@ -523,12 +516,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    from paper_1210_4090_gb300 import dist as D
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, _ = D.reduce_step(float(sum(step_ms)), 0.0, dev)
     ms_per_step = total_ms / args.steps
     updates = p.npts * p.nsteps
     value = world * updates * args.steps / (total_ms * 1e-3)

@@ -10,7 +10,7 @@ compiled library.
 """
 import importlib
 
-__all__ = ["hjlo", "workloads"]
+__all__ = ["hjlo", "workloads", "dist", "autograd"]
 
 
 def __getattr__(name):

@@ -260,18 +260,20 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         if (d->algo == HJLO_ALGO_AUTO && (ax.weff < 8 || !(ax.curv > 0))) algo = KALGO_BRUTE;
         if (algo != KALGO_MONGE) all_monge = false;
         s = shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
+        apply_test_knobs(ax);
+        if (s == HJLO_OK) s = dmalloc((void **)&ax.d_kr64, sizeof(double) * ax.weff, "cudaMalloc(kernel table)");
         if (s == HJLO_OK) {
-            cudaError_t e = cudaMalloc(&ax.d_kr64, sizeof(double) * ax.weff);
-            if (e == cudaSuccess) e = cudaMemcpy(ax.d_kr64, k64, sizeof(double) * ax.weff, cudaMemcpyHostToDevice);
+            cudaError_t e = cudaMemcpy(ax.d_kr64, k64, sizeof(double) * ax.weff, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) s = cuda_error(e, "kernel table upload");
         }
         free(k64);
         if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
     }
     p->algo = all_monge ? HJLO_ALGO_MONGE : HJLO_ALGO_BRUTE;
-    cudaError_t e = cudaMalloc(&p->d_counters, sizeof(unsigned long long) * CNT_N);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_flags, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(p->d_counters, 0, sizeof(unsigned long long) * CNT_N);
+    s = dmalloc((void **)&p->d_counters, sizeof(unsigned long long) * CNT_N, "cudaMalloc(counters)");
+    if (s == HJLO_OK) s = dmalloc((void **)&p->d_flags, sizeof(int), "cudaMalloc(flags)");
+    if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
+    cudaError_t e = cudaMemset(p->d_counters, 0, sizeof(unsigned long long) * CNT_N);
     if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { s = cuda_error(e, "plan allocation"); hjlo_plan_destroy(p); return s; }

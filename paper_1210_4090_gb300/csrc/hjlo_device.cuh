@@ -75,7 +75,8 @@ struct PassParams {
     double kmax;              // max |k| over the window
     double curv;              // lower bound of the min second difference of k (inf if weff < 3)
     int off_u, off_fx, off_kfx, off_t, off_k64, off_misc;  // shared memory offsets (bytes)
-    long long wait_ns;        // bound on every mbarrier wait
+    long long wait_ns;        // bound on the first mbarrier wait of a tile
+    int test_extra_tx;        // test knob: bytes the barrier expects beyond the copy (0 in use)
     double hscale;            // hv_scaled: potential term fl(m - fl(hscale * hv[x]))
     int hv_scaled;            // 0: hv already holds h*V
 };
@@ -406,11 +407,11 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         if (tid == 0) {
             if (LAYOUT == LAYOUT_CONTIG) {
                 uint32_t bytes = (uint32_t)((long long)tl.valid * N * (long long)sizeof(T));
-                mbar_arrive_expect_tx(bar, bytes);
+                mbar_arrive_expect_tx(bar, bytes + (uint32_t)p.test_extra_tx);
                 tma_bulk_load(su, src + tl.base, bytes, bar);
             } else {
                 uint32_t bytes = (uint32_t)(p.nbox * p.by * C * (int)sizeof(T));
-                mbar_arrive_expect_tx(bar, bytes);
+                mbar_arrive_expect_tx(bar, bytes + (uint32_t)p.test_extra_tx);
                 long long o = tile / p.tiles_per_outer;
                 int x0 = (int)((tile - o * p.tiles_per_outer) << p.log2C);
                 for (int b = 0; b < p.nbox; ++b)
@@ -429,7 +430,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             // the copy did not land in time: flag it, give it one more bounded
             // wait so nothing is still writing our shared memory, and leave
             if (tid == 0) atomicOr(p.flags, FLAG_TIMEOUT);
-            mbar_wait_bounded(bar, 0, p.wait_ns);
+            mbar_wait_bounded(bar, 0, 500000000LL);
             return;
         }
     } else {

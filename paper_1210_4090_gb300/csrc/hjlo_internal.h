@@ -25,6 +25,8 @@ struct AxisPlan {
     int C = 1, log2C = 0, wpl = 1, threads = 32;
     int lpl = 32, log2lpl = 5, seg = 1;   // MONGE: lanes per line, odd segment
     int gs = 1, tp = 2;                    // MONGE pivot group; argmin row pitch
+    long long wait_ns = 500000000LL;       // first TMA wait bound (0.5 s)
+    int test_extra_tx = 0;                 // test knob, see apply_test_knobs
     int by = 1, nbox = 1, lp = 0;
     long long ntiles = 0, tiles_per_outer = 1;
     size_t smem = 0;
@@ -58,6 +60,16 @@ hjlo_status launch_pass_batch(const AxisPlan &ax, int dtype, const BatchItem *d_
 hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *dst, const double *hv,
                         double hv_scale, int32_t *amin, unsigned long long *counters, int *flags,
                         cudaStream_t st);
+
+// Device allocation through one place, so tests can inject failures
+// (HJLO_TEST_FAIL_ALLOC=k makes the k-th allocation of the process fail).
+hjlo_status dmalloc(void **ptr, size_t bytes, const char *what);
+
+// Test knobs read when a plan is created (never set in normal use):
+// HJLO_TEST_EXTRA_TX=b makes every TMA barrier expect b bytes more than its
+// copy delivers, so the bounded wait runs out (HJLO_ETIMEOUT);
+// HJLO_TEST_WAIT_NS=n shortens the first wait to n ns.
+void apply_test_knobs(AxisPlan &ax);
 
 // One-time per-device kernel attributes; call outside stream capture.
 hjlo_status prepare_kernels();

@@ -12,6 +12,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cmath>
 #include <cstdarg>
@@ -396,7 +397,36 @@ static void fill_params(const AxisPlan &ax, PassParams &p)
     p.off_t = ax.off_t;
     p.off_k64 = ax.off_k64;
     p.off_misc = ax.off_misc;
-    p.wait_ns = 500000000LL;   // 0.5 s: a tile copy takes microseconds
+    p.wait_ns = ax.wait_ns;    // 0.5 s unless a test shortens it: a tile copy takes microseconds
+    p.test_extra_tx = ax.test_extra_tx;
+}
+
+hjlo_status dmalloc(void **ptr, size_t bytes, const char *what)
+{
+    static std::atomic<long long> counter{0};
+    static long long fail_at = -1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *e = getenv("HJLO_TEST_FAIL_ALLOC");
+        fail_at = e ? atoll(e) : -1;
+    });
+    *ptr = nullptr;
+    long long k = ++counter;
+    if (fail_at > 0 && k == fail_at) return set_error(HJLO_ENOMEM, "%s: injected allocation failure", what);
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return cuda_error(e, what);
+    }
+    return HJLO_OK;
+}
+
+void apply_test_knobs(AxisPlan &ax)
+{
+    const char *e = getenv("HJLO_TEST_EXTRA_TX");
+    ax.test_extra_tx = e ? std::max(0, atoi(e)) : 0;
+    e = getenv("HJLO_TEST_WAIT_NS");
+    if (e) ax.wait_ns = std::max(0LL, atoll(e));
 }
 
 hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *dst, const double *hv,
