@@ -132,7 +132,9 @@ hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
 /*
  * One time step (eq. eqconvol): u_out = T(u_in).  u_in and u_out hold npts
  * values of the plan's dtype and may be the same pointer (in place).  V: npts
- * binary64 values of V(t_n, .) or NULL for V = 0.  argmin_out: NULL, or
+ * binary64 values of V(t_n, .) or NULL for V = 0; V must not overlap u_in,
+ * u_out or argmin_out (it is read through the read-only cache while the
+ * outputs are written).  argmin_out: NULL, or
  * ndim*npts int32 receiving the argmin displacement d of every pass, laid out
  * [axis][point] (the discrete optimal path of eq. raslebol, one step).
  */

@@ -39,7 +39,7 @@ def sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".inc"))]
     files.append(os.path.join(INCLUDE, "hjlo.h"))
     return files
 

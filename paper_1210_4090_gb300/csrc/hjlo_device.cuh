@@ -79,6 +79,8 @@ struct PassParams {
     int test_extra_tx;        // test knob: bytes the barrier expects beyond the copy (0 in use)
     double hscale;            // hv_scaled: potential term fl(m - fl(hscale * hv[x]))
     int hv_scaled;            // 0: hv already holds h*V
+    int wide_mul, wide_add;   // MONGE: a bracket of more than wide_mul * (expected span) + wide_add
+                              // offsets is searched by the whole warp
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -156,6 +158,20 @@ __device__ __forceinline__ void tma_tensor_load_3d(void *dst, const CUtensorMap 
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
         "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Hint: bring [p, p + bytes) of global memory into L2 ahead of use (whole
+// 16-byte units inside the range only; the ragged ends load normally).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned long long bytes)
+{
+    const unsigned long long a = (unsigned long long)__cvta_generic_to_global(p);
+    unsigned long long s = (a + 15ull) & ~15ull;
+    const unsigned long long e = (a + bytes) & ~15ull;
+    while (s < e) {
+        const unsigned long long n = (e - s < (1ull << 20)) ? e - s : (1ull << 20);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)n) : "memory");
+        s += n;
+    }
 }
 
 // ------------------------------------------------------------------ number helpers
@@ -339,23 +355,96 @@ __device__ __forceinline__ int screened_row(const PassParams &p, const T *su, co
     return bt;
 }
 
-// One output: the binary64 add of the kept candidate, the potential term and
-// the stores.
+// Search of one row per lane with offload: lanes whose bracket [tlo, thi]
+// is at least `wide` offsets long (rows next to a shock of the argmin map)
+// hand their rows to the warp, which splits into k groups of 32/k lanes
+// (k = the number of such rows, rounded up to a power of two) that search
+// them side by side; the other lanes scan their own rows first.  Each group
+// returns what the sequential screened_row returns (smallest screened value,
+// first offset on ties; binary64 re-scan of the survivors when a second
+// candidate is within the screen's error).  Every lane of the warp must call
+// it (has = false for lanes without a row).  Returns this lane's offset.
 template <typename T, int LAYOUT>
-__device__ __forceinline__ void finish_point(const PassParams &p, const Tile<LAYOUT> &tl, const T *su,
-                                             const unsigned short *tt, const double *kr64, T *dst, int l, int i)
+__device__ __forceinline__ int row_or_offload(const PassParams &p, const T *su, const int *fx, const int *kfx,
+                                              const double *kr64, int line, int r, int tlo, int thi,
+                                              int thr_add, bool has, int wide, int &rescans)
 {
-    const int N = (int)p.N;
-    int t = tt[l * p.tp + i];
-    int pos = wrapN(i + t + p.hoff, N);
-    double m = __dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[t]);
-    long long x = tl.base + l * tl.lstride + (long long)i * tl.pstride;
-    if (p.hv) {
-        double hv = p.hv_scaled ? __dmul_rn(p.hscale, p.hv[x]) : p.hv[x];
-        m = __dsub_rn(m, hv);
+    const bool longj = has && (thi - tlo >= wide);
+    int t = 0;
+    if (has && !longj)
+        t = screened_row<T, LAYOUT>(p, su, fx + line * p.lp + r, kfx + line * p.weff, kr64, line, r, tlo, thi,
+                                    thr_add, rescans);
+    const unsigned mask = __ballot_sync(0xffffffffu, longj);
+    if (mask == 0u) return t;
+    const int lane = threadIdx.x & 31;
+    const int k = __popc(mask);
+    int lgG = 5;                                   // group size G = 2^lgG = 32 / next_pow2(k)
+    while ((1 << (5 - lgG)) < k) --lgG;
+    const int G = 1 << lgG;
+    const int job = lane >> lgG, sl = lane & (G - 1);
+    const bool gact = job < k;
+    // the lane holding the job-th long row
+    unsigned m = mask;
+    for (int i = 0; i < job && m; ++i) m &= m - 1;
+    const int src = (gact && m) ? __ffs(m) - 1 : lane;
+    const int rb = __shfl_sync(0xffffffffu, r, src);
+    const int lob = __shfl_sync(0xffffffffu, tlo, src);
+    const int hib = __shfl_sync(0xffffffffu, thi, src);
+    const int lnb = __shfl_sync(0xffffffffu, line, src);
+    const int thb = __shfl_sync(0xffffffffu, thr_add, src);
+    const int *f = fx + lnb * p.lp + rb;
+    const int *kk = kfx + lnb * p.weff;
+    int m1 = 0x7fffffff, m2 = 0x7fffffff, t1 = 0x7fffffff;
+    if (gact) {
+        for (int tt = lob + sl; tt <= hib; tt += G) {
+            const int c = f[tt] + kk[tt];
+            m2 = min(m2, max(m1, c));
+            t1 = (c < m1) ? tt : t1;
+            m1 = min(m1, c);
+        }
     }
-    store_val(dst + x, m);
-    if (p.amin) p.amin[x] = p.dhi - t;
+    for (int w = G >> 1; w; w >>= 1) {
+        const int om1 = __shfl_xor_sync(0xffffffffu, m1, w);
+        const int om2 = __shfl_xor_sync(0xffffffffu, m2, w);
+        const int ot1 = __shfl_xor_sync(0xffffffffu, t1, w);
+        const int nm2 = min(max(m1, om1), min(m2, om2));
+        if (om1 < m1 || (om1 == m1 && ot1 < t1)) { m1 = om1; t1 = ot1; }
+        m2 = nm2;
+    }
+    const int thr = gact ? m1 + thb : 0;
+    const bool need = gact && !(m2 > thr);
+    int res = t1;
+    if (__any_sync(0xffffffffu, need)) {
+        const int N = (int)p.N;
+        unsigned long long bk = ~0ull;
+        int bt = 0x7fffffff;
+        if (need) {
+            for (int tt = lob + sl; tt <= hib; tt += G) {
+                if (f[tt] + kk[tt] <= thr) {
+                    const int pos = wrapN(rb + tt + p.hoff, N);
+                    const double e = __dadd_rn(widen(su[uidx<LAYOUT>(p, lnb, pos)]), kr64[tt]);
+                    const unsigned long long key = dkey(e);
+                    if (key < bk) { bk = key; bt = tt; }
+                }
+            }
+        }
+        for (int w = G >> 1; w; w >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, w);
+            const int ot = __shfl_xor_sync(0xffffffffu, bt, w);
+            if (ok < bk || (ok == bk && ot < bt)) { bk = ok; bt = ot; }
+        }
+        if (need) res = bt;
+    }
+    // the owner of the j-th long row reads lane j * G (its group's first lane)
+    const int rank = __popc(mask & ((1u << lane) - 1u));
+    const int from = longj ? (rank << lgG) : lane;
+    const int got = __shfl_sync(0xffffffffu, res, from);
+    const int gneed = __shfl_sync(0xffffffffu, need ? 1 : 0, from);
+    if (longj) {
+        t = got;
+        rescans += gneed;
+    }
+    return t;
 }
 
 // ------------------------------------------------------------------ the pass kernel
@@ -423,6 +512,10 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             for (int i = tid; i < N; i += nthr)
                 su[uidx<LAYOUT>(p, l, i)] = src[tl.base + l * tl.lstride + (long long)i * tl.pstride];
     }
+    // the potential term of a contiguous tile is read at the very end: start
+    // moving it towards L2 now, behind the search
+    if (LAYOUT == LAYOUT_CONTIG && p.hv && tid == nthr - 1)
+        prefetch_l2(p.hv + tl.base, (unsigned long long)tl.valid * N * sizeof(double));
     for (int i = tid; i < weff; i += nthr) kr64[i] = p.kr64[i];
     if (p.use_tma) {
         bool ok = mbar_wait_bounded(bar, 0, p.wait_ns);
@@ -511,8 +604,8 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 int pos = (sub + p.hoff) % N;
                 for (int jj = sub; jj < L; jj += lpl) {
                     lfx[jj] = (int)(fixq32(widen(lu[pos]), q) - fref);
-                    pos += lpl;
-                    while (pos >= N) pos -= N;
+                    pos += lpl;                      // lpl <= N
+                    pos = (pos >= N) ? pos - N : pos;
                 }
                 for (int t = sub; t < weff; t += lpl) kfx[cl * weff + t] = (int)fixq32(kr64[t], q);
             }
@@ -522,9 +615,14 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 const int q = li[l].q;
                 const unsigned fref = li[l].fref;
                 const int step = nthr >> p.log2C;
-                for (int jj = tid >> p.log2C; jj < L; jj += step) {
-                    int pos = wrapN(jj + p.hoff, N);
-                    fx[l * p.lp + jj] = (int)(fixq32(widen(su[(pos << p.log2C) + l]), q) - fref);
+                int *lfx = fx + l * p.lp;
+                int jj = tid >> p.log2C;
+                int pos = (jj + p.hoff) % N;
+                const int stepN = step % N;
+                for (; jj < L; jj += step) {
+                    lfx[jj] = (int)(fixq32(widen(su[(pos << p.log2C) + l]), q) - fref);
+                    pos += stepN;
+                    pos = (pos >= N) ? pos - N : pos;
                 }
                 for (int t = tid >> p.log2C; t < weff; t += step) kfx[l * weff + t] = (int)fixq32(kr64[t], q);
             }
@@ -618,35 +716,52 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             if (hp && o == 0) lt[rp] = (unsigned short)tpiv;
             __syncthreads();
             // P2: the other segments' first rows, bracketed by the argmins of
-            // this group's and the next group's pivot rows
-            if (work && o != 0 && s0 < s1) {
-                const int jl = rp + lt[rp];
-                const int rn = min((g - o + GS) * S, N);
-                const int jr = (rn < N) ? rn + lt[rn] : N + lt[0];
-                int lo = max(jl - s0, 0), hi = min(jr - s0, weff - 1);
-                if (lo > hi) { lo = 0; hi = weff - 1; }   // never for a Monge matrix
-                lt[s0] = (unsigned short)screened_row<T, LAYOUT>(p, su, lfx + s0, lk, kr64, line, s0, lo, hi,
-                                                                thr_add, rescans);
+            // this group's and the next group's pivot rows (about GS * S
+            // offsets away from shocks; wider brackets go to the warp)
+            {
+                const bool has = work && o != 0 && s0 < s1;
+                int lo = 0, hi = 0;
+                if (has) {
+                    const int jl = rp + lt[rp];
+                    const int rn = min((g - o + GS) * S, N);
+                    const int jr = (rn < N) ? rn + lt[rn] : N + lt[0];
+                    lo = max(jl - s0, 0);
+                    hi = min(jr - s0, weff - 1);
+                    if (lo > hi) { lo = 0; hi = weff - 1; }   // never for a Monge matrix
+                }
+                const int t = row_or_offload<T, LAYOUT>(p, su, fx, kfx, kr64, lsafe, s0, lo, hi, thr_add, has,
+                                                        p.wide_mul * GS * S + p.wide_add, rescans);
+                if (has) lt[s0] = (unsigned short)t;
             }
             __syncthreads();
         }
-        // P3: the rest of each segment by divide and conquer
-        if (work && s1 - s0 >= 2) {
-            // right bracket: the next segment's first row, or the first row
-            // shifted by one period
-            const int jnext = (s1 < N) ? (s1 + lt[s1]) : (N + lt[0]);
-            const int Sg = s1 - s0;
+        // P3: the rest of each segment by divide and conquer; right
+        // bracket: the next segment's first row, or the first row shifted by
+        // one period
+        {
+            // every lane walks the block-uniform segment length S (rows past
+            // its segment's end are predicated off)
+            const bool dc = work && s1 - s0 >= 2;
+            const int jnext = dc ? ((s1 < N) ? (s1 + lt[s1]) : (N + lt[0])) : 0;
+            const int nr = s1 - s0;
             int step = 1;
-            while (step * 2 < Sg) step *= 2;
+            while (step * 2 < S) step *= 2;
             for (; step >= 1; step >>= 1) {
-                for (int r = s0 + step; r < s1; r += 2 * step) {
-                    int jl = (r - step) + lt[r - step];
-                    int qq = r + step;
-                    int jr = (qq < s1) ? qq + lt[qq] : jnext;
-                    int tlo = max(jl - r, 0), thi = min(jr - r, weff - 1);
-                    if (tlo > thi) { tlo = 0; thi = weff - 1; }   // never for a Monge matrix
-                    lt[r] = (unsigned short)screened_row<T, LAYOUT>(p, su, lfx + r, lk, kr64, line, r, tlo, thi,
-                                                                   thr_add, rescans);
+                for (int rr = step; rr < S; rr += 2 * step) {
+                    const bool has = dc && rr < nr;
+                    const int r = s0 + rr;
+                    int tlo = 0, thi = 0;
+                    if (has) {
+                        const int jl = (r - step) + lt[r - step];
+                        const int qq = r + step;
+                        const int jr = (qq < s1) ? qq + lt[qq] : jnext;
+                        tlo = max(jl - r, 0);
+                        thi = min(jr - r, weff - 1);
+                        if (tlo > thi) { tlo = 0; thi = weff - 1; }   // never for a Monge matrix
+                    }
+                    const int t = row_or_offload<T, LAYOUT>(p, su, fx, kfx, kr64, lsafe, r, tlo, thi, thr_add, has,
+                                                            p.wide_mul * (2 * step + 1) + p.wide_add, rescans);
+                    if (has) lt[r] = (unsigned short)t;
                 }
             }
         }
@@ -687,13 +802,57 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     if (LAYOUT == LAYOUT_CONTIG) {
         const int lanes = nthr >> p.log2C;              // threads per line
         const int l = tid / lanes, sub = tid - l * lanes;
-        if (l < tl.valid)
-            for (int i = sub; i < N; i += lanes) finish_point<T, LAYOUT>(p, tl, su, tt, kr64, dst, l, i);
+        if (l < tl.valid) {
+            const unsigned short *lt = tt + l * p.tp;
+            const T *lu = su + l * N;
+            const long long xb = tl.base + l * tl.lstride;
+            T *gd = dst + xb;
+            const double *gh = p.hv ? p.hv + xb : nullptr;
+            int32_t *ga = p.amin ? p.amin + xb : nullptr;
+            // four outputs per thread at a time, their potential-term loads
+            // issued together
+            int i = sub;
+            for (; i + 3 * lanes < N; i += 4 * lanes) {
+                double hvb[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) hvb[b] = gh ? __ldg(gh + i + b * lanes) : 0.0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int ii = i + b * lanes;
+                    const int t = lt[ii];
+                    const int pos = wrapN(ii + t + p.hoff, N);
+                    double m = __dadd_rn(widen(lu[pos]), kr64[t]);
+                    if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, hvb[b]) : hvb[b]);
+                    store_val(gd + ii, m);
+                    if (ga) ga[ii] = p.dhi - t;
+                }
+            }
+            for (; i < N; i += lanes) {
+                const int t = lt[i];
+                const int pos = wrapN(i + t + p.hoff, N);
+                double m = __dadd_rn(widen(lu[pos]), kr64[t]);
+                if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, gh[i]) : gh[i]);
+                store_val(gd + i, m);
+                if (ga) ga[i] = p.dhi - t;
+            }
+        }
     } else {
-        const int total = C * N;
-        for (int idx = tid; idx < total; idx += nthr) {
-            int i = idx >> p.log2C, l = idx & (C - 1);
-            if (l < tl.valid) finish_point<T, LAYOUT>(p, tl, su, tt, kr64, dst, l, i);
+        const int l = tid & (C - 1);
+        if (l < tl.valid) {
+            const int step = nthr >> p.log2C;
+            const unsigned short *lt = tt + l * p.tp;
+            const long long xb = tl.base + l;
+            const long long xs = (long long)step * tl.pstride;
+            int i = tid >> p.log2C;
+            long long x = xb + (long long)i * tl.pstride;
+            for (; i < N; i += step, x += xs) {
+                const int t = lt[i];
+                const int pos = wrapN(i + t + p.hoff, N);
+                double m = __dadd_rn(widen(su[(pos << p.log2C) + l]), kr64[t]);
+                if (p.hv) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, p.hv[x]) : p.hv[x]);
+                store_val(dst + x, m);
+                if (p.amin) p.amin[x] = p.dhi - t;
+            }
         }
     }
     if (ALGO == KALGO_MONGE && tid == 0) {

@@ -27,6 +27,7 @@ struct AxisPlan {
     int gs = 1, tp = 2;                    // MONGE pivot group; argmin row pitch
     long long wait_ns = 500000000LL;       // first TMA wait bound (0.5 s)
     int test_extra_tx = 0;                 // test knob, see apply_test_knobs
+    int wide_mul = 2, wide_add = 8;        // warp offload of wide brackets (see PassParams)
     int by = 1, nbox = 1, lp = 0;
     long long ntiles = 0, tiles_per_outer = 1;
     size_t smem = 0;
@@ -70,6 +71,25 @@ hjlo_status dmalloc(void **ptr, size_t bytes, const char *what);
 // copy delivers, so the bounded wait runs out (HJLO_ETIMEOUT);
 // HJLO_TEST_WAIT_NS=n shortens the first wait to n ns.
 void apply_test_knobs(AxisPlan &ax);
+
+// Kernel instantiations, one translation unit per storage type and layout
+// (hjlo_kern_*.cu): shared-memory opt-in and launchers.
+hjlo_status kern_allow_smem_f64_contig();
+hjlo_status kern_single_f64_contig(const AxisPlan &ax, const CUtensorMap &map, const PassParams &p, cudaStream_t st);
+hjlo_status kern_batch_f64_contig(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
+                             cudaStream_t st);
+hjlo_status kern_allow_smem_f64_strided();
+hjlo_status kern_single_f64_strided(const AxisPlan &ax, const CUtensorMap &map, const PassParams &p, cudaStream_t st);
+hjlo_status kern_batch_f64_strided(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
+                             cudaStream_t st);
+hjlo_status kern_allow_smem_f32_contig();
+hjlo_status kern_single_f32_contig(const AxisPlan &ax, const CUtensorMap &map, const PassParams &p, cudaStream_t st);
+hjlo_status kern_batch_f32_contig(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
+                             cudaStream_t st);
+hjlo_status kern_allow_smem_f32_strided();
+hjlo_status kern_single_f32_strided(const AxisPlan &ax, const CUtensorMap &map, const PassParams &p, cudaStream_t st);
+hjlo_status kern_batch_f32_strided(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
+                             cudaStream_t st);
 
 // One-time per-device kernel attributes; call outside stream capture.
 hjlo_status prepare_kernels();

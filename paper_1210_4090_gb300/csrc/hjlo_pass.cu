@@ -234,13 +234,29 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
             pivot_group(ax.weff, S, lpl, &pcost);
             double work = pcost / S + std::log2((double)S) + 3.0;
             double score = eff / work;
-            if (env && atoi(env) == lpl) { best_lpl = lpl; break; }
+            if (env && atoi(env) == lpl && lpl <= N) { best_lpl = lpl; break; }
             if (S >= 3 && score > best_score * 1.0001) { best_score = score; best_lpl = lpl; }
         }
+        // staging and write-back assume every lane of a line owns at most one
+        // point per sweep of lpl, i.e. lpl <= N
+        if (best_lpl > N) best_lpl = 1;
         ax.lpl = best_lpl;
         ax.log2lpl = ilog2(best_lpl);
         ax.seg = odd_at_least((N + best_lpl - 1) / best_lpl);
         ax.gs = pivot_group(ax.weff, ax.seg, ax.lpl, nullptr);
+        // tuning override "mul,add" of the offload rule; "0" turns it off
+        ax.wide_mul = 2;
+        ax.wide_add = 8;
+        if (const char *e = getenv("HJLO_OFFLOAD")) {
+            int m = 0, a = 0;
+            if (sscanf(e, "%d,%d", &m, &a) == 2 && m >= 0 && a >= 0) {
+                ax.wide_mul = m;
+                ax.wide_add = a;
+            } else {
+                ax.wide_mul = 0;
+                ax.wide_add = 1 << 24;
+            }
+        }
         ax.lp = halo_pitch(ax);
         ax.wpl = 1;
     } else {
@@ -321,17 +337,6 @@ bool encode_strided(const AxisPlan &ax, int esize, const void *ptr, CUtensorMap 
 
 // ------------------------------------------------------------------ launch
 
-template <typename T, int LAYOUT, int ALGO>
-static hjlo_status allow_smem()
-{
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<T, LAYOUT, ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(pass_kernel_batch<T, LAYOUT, ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024);
-    return e == cudaSuccess ? HJLO_OK : cuda_error(e, "cudaFuncSetAttribute");
-}
-
 // Per-device one-time set-up done outside any stream capture: shared-memory
 // opt-in of every pass kernel and the driver entry point for TMA descriptors.
 hjlo_status prepare_kernels()
@@ -344,26 +349,32 @@ hjlo_status prepare_kernels()
     std::lock_guard<std::mutex> g(mu);
     if (dev < 64 && done[dev]) return HJLO_OK;
     hjlo_status s;
-    if ((s = allow_smem<double, LAYOUT_CONTIG, KALGO_BRUTE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<double, LAYOUT_CONTIG, KALGO_MONGE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<double, LAYOUT_STRIDED, KALGO_BRUTE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<double, LAYOUT_STRIDED, KALGO_MONGE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<float, LAYOUT_CONTIG, KALGO_BRUTE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<float, LAYOUT_CONTIG, KALGO_MONGE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<float, LAYOUT_STRIDED, KALGO_BRUTE>()) != HJLO_OK) return s;
-    if ((s = allow_smem<float, LAYOUT_STRIDED, KALGO_MONGE>()) != HJLO_OK) return s;
+    if ((s = kern_allow_smem_f64_contig()) != HJLO_OK) return s;
+    if ((s = kern_allow_smem_f64_strided()) != HJLO_OK) return s;
+    if ((s = kern_allow_smem_f32_contig()) != HJLO_OK) return s;
+    if ((s = kern_allow_smem_f32_strided()) != HJLO_OK) return s;
     encode_fn();
     if (dev < 64) done[dev] = true;
     return HJLO_OK;
 }
 
-template <typename T, int LAYOUT, int ALGO>
-static hjlo_status launch_t(const AxisPlan &ax, const CUtensorMap &map, const PassParams &p, cudaStream_t st)
+static hjlo_status dispatch_single(const AxisPlan &ax, int dtype, const CUtensorMap &map, const PassParams &p,
+                                   cudaStream_t st)
 {
-    pass_kernel<T, LAYOUT, ALGO><<<(unsigned)ax.ntiles, ax.threads, ax.smem, st>>>(map, p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "pass kernel launch");
-    return HJLO_OK;
+    const bool strided = (ax.layout == LAYOUT_STRIDED);
+    if (dtype == HJLO_F64)
+        return strided ? kern_single_f64_strided(ax, map, p, st) : kern_single_f64_contig(ax, map, p, st);
+    return strided ? kern_single_f32_strided(ax, map, p, st) : kern_single_f32_contig(ax, map, p, st);
+}
+
+static hjlo_status dispatch_batch(const AxisPlan &ax, int dtype, const BatchItem *items, const PassParams &p,
+                                  long long count, cudaStream_t st)
+{
+    const bool strided = (ax.layout == LAYOUT_STRIDED);
+    if (dtype == HJLO_F64)
+        return strided ? kern_batch_f64_strided(ax, items, p, count, st)
+                       : kern_batch_f64_contig(ax, items, p, count, st);
+    return strided ? kern_batch_f32_strided(ax, items, p, count, st) : kern_batch_f32_contig(ax, items, p, count, st);
 }
 
 static void fill_params(const AxisPlan &ax, PassParams &p)
@@ -399,6 +410,8 @@ static void fill_params(const AxisPlan &ax, PassParams &p)
     p.off_misc = ax.off_misc;
     p.wait_ns = ax.wait_ns;    // 0.5 s unless a test shortens it: a tile copy takes microseconds
     p.test_extra_tx = ax.test_extra_tx;
+    p.wide_mul = ax.wide_mul;
+    p.wide_add = ax.wide_add;
 }
 
 hjlo_status dmalloc(void **ptr, size_t bytes, const char *what)
@@ -451,32 +464,9 @@ hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *ds
     } else {
         p.use_tma = encode_strided(ax, esize, src, &map) ? 1 : 0;
     }
-    const bool f64 = (dtype == HJLO_F64);
-    const bool strided = (ax.layout == LAYOUT_STRIDED);
-    const bool monge = (ax.algo == KALGO_MONGE);
-    if (f64) {
-        if (strided) return monge ? launch_t<double, LAYOUT_STRIDED, KALGO_MONGE>(ax, map, p, st)
-                                  : launch_t<double, LAYOUT_STRIDED, KALGO_BRUTE>(ax, map, p, st);
-        return monge ? launch_t<double, LAYOUT_CONTIG, KALGO_MONGE>(ax, map, p, st)
-                     : launch_t<double, LAYOUT_CONTIG, KALGO_BRUTE>(ax, map, p, st);
-    }
-    if (strided) return monge ? launch_t<float, LAYOUT_STRIDED, KALGO_MONGE>(ax, map, p, st)
-                              : launch_t<float, LAYOUT_STRIDED, KALGO_BRUTE>(ax, map, p, st);
-    return monge ? launch_t<float, LAYOUT_CONTIG, KALGO_MONGE>(ax, map, p, st)
-                 : launch_t<float, LAYOUT_CONTIG, KALGO_BRUTE>(ax, map, p, st);
+    return dispatch_single(ax, dtype, map, p, st);
 }
 
-template <typename T, int LAYOUT, int ALGO>
-static hjlo_status launch_b(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
-                            cudaStream_t st)
-{
-    long long blocks = ax.ntiles * count;
-    if (blocks > 0x7fffffffLL) return set_error(HJLO_EUNSUPPORTED, "batched launch too large");
-    pass_kernel_batch<T, LAYOUT, ALGO><<<(unsigned)blocks, ax.threads, ax.smem, st>>>(items, p, count);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "batched pass kernel launch");
-    return HJLO_OK;
-}
 
 hjlo_status launch_pass_batch(const AxisPlan &ax, int dtype, const BatchItem *d_items, long long count,
                               unsigned long long *counters, int *flags, cudaStream_t st)
@@ -485,19 +475,7 @@ hjlo_status launch_pass_batch(const AxisPlan &ax, int dtype, const BatchItem *d_
     fill_params(ax, p);
     p.counters = counters;
     p.flags = flags;
-    const bool f64 = (dtype == HJLO_F64);
-    const bool strided = (ax.layout == LAYOUT_STRIDED);
-    const bool monge = (ax.algo == KALGO_MONGE);
-    if (f64) {
-        if (strided) return monge ? launch_b<double, LAYOUT_STRIDED, KALGO_MONGE>(ax, d_items, p, count, st)
-                                  : launch_b<double, LAYOUT_STRIDED, KALGO_BRUTE>(ax, d_items, p, count, st);
-        return monge ? launch_b<double, LAYOUT_CONTIG, KALGO_MONGE>(ax, d_items, p, count, st)
-                     : launch_b<double, LAYOUT_CONTIG, KALGO_BRUTE>(ax, d_items, p, count, st);
-    }
-    if (strided) return monge ? launch_b<float, LAYOUT_STRIDED, KALGO_MONGE>(ax, d_items, p, count, st)
-                              : launch_b<float, LAYOUT_STRIDED, KALGO_BRUTE>(ax, d_items, p, count, st);
-    return monge ? launch_b<float, LAYOUT_CONTIG, KALGO_MONGE>(ax, d_items, p, count, st)
-                 : launch_b<float, LAYOUT_CONTIG, KALGO_BRUTE>(ax, d_items, p, count, st);
+    return dispatch_batch(ax, dtype, d_items, p, count, st);
 }
 
 hjlo_status device_facts(DeviceFacts &f)

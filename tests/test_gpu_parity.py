@@ -264,3 +264,28 @@ def test_full_size_sampled(wl, checkpoints, count):
     cnt = plan.sync()
     assert cnt["error_flags"] == 0 and cnt["steps"] == p.nsteps
     assert np.isfinite(u.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("lanes", [0, 2, 4, 8, 16, 32, 64], ids=lambda v: "lpl%d" % v if v else "auto")
+@pytest.mark.parametrize("offload", ["", "0", "0,2"], ids=["offload-default", "offload-off", "offload-all"])
+def test_segment_shapes_with_shocks(lanes, offload, monkeypatch):
+    """Every segment length the monotone search can take (lanes per line forced
+    from the environment), with the warp offload of wide brackets at its
+    default rule, turned off, and taking every bracket of two or more offsets
+    (groups of every size), on a developed solution with shocks (wide argmin
+    jumps) and on a rough start (wide brackets everywhere)."""
+    if lanes:
+        monkeypatch.setenv("HJLO_LANES_PER_LINE", str(lanes))
+    if offload:
+        monkeypatch.setenv("HJLO_OFFLOAD", offload)
+    p = WL.grid1024(N=160, nsteps=60, W=12)
+    ref = O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, p.nsteps)
+    got, _, cnt = gpu_run(p.shape, p.dx, p.h, p.P, p.W, p.u0, p.V, p.nsteps, algo=2)
+    assert cnt["error_flags"] == 0
+    assert np.array_equal(got.view(np.int64), ref.view(np.int64))
+    shape, dx, h, P, W = (24, 200), (1 / 24, 1 / 200), 0.05, (0.3, -0.2), (4, 40)
+    u0, V = gen(shape, 17, scale=1.0)
+    ref, ref_am = O.run(u0, dx, h, P, W, V, 2, record_argmin=True)
+    got, am, _ = gpu_run(shape, dx, h, P, W, u0, V, 2, algo=2, argmin=True)
+    assert np.array_equal(got.view(np.int64), ref.view(np.int64))
+    assert np.array_equal(am, ref_am)
