@@ -269,8 +269,10 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
     }
     const int lanes = (algo == KALGO_MONGE) ? ax.lpl : 32 * ax.wpl;
     // lines per CTA: at least one warp of threads, TMA-friendly for strided
-    // lines, up to 512 threads while tiles stay >= 2 per SM and the shared
-    // memory fits twice per SM
+    // lines, then grown while tiles stay >= 2 per SM and the shared memory
+    // fits twice per SM, up to 128 threads for the monotone search (small
+    // tiles balance the SMs best; measured on the 1024^2 and 256^3 grids)
+    // and 512 for brute force
     int C = std::max(cmin, std::max(1, 32 / lanes));
     while (C < cmin) C *= 2;
     auto tiles_for = [&](int c) -> long long {
@@ -282,13 +284,24 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
     if (ax.smem > smem_optin || (long long)C * lanes > 1024)
         return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit in shared memory", N);
     const size_t budget = 110 * 1024;
-    while (2 * C <= std::max(cmax, C) && (long long)2 * C * lanes <= 512 &&
+    const long long cap = (algo == KALGO_MONGE) ? 128 : 512;
+    while (2 * C <= std::max(cmax, C) && (long long)2 * C * lanes <= cap &&
            tiles_for(2 * C) * std::max(1LL, replicas) >= 2LL * num_sms) {
         AxisPlan t = ax;
         t.C = 2 * C;
         layout_smem(t, esize, algo);
         if (t.smem > budget) break;
         C *= 2;
+    }
+    // tuning override of the lines per tile (a power of two that fits)
+    if (const char *e = getenv("HJLO_LINES_PER_TILE")) {
+        const int want = atoi(e);
+        if (want >= cmin && (want & (want - 1)) == 0 && (long long)want * lanes <= 1024) {
+            AxisPlan t = ax;
+            t.C = want;
+            layout_smem(t, esize, algo);
+            if (t.smem <= smem_optin) C = want;
+        }
     }
     ax.C = C;
     ax.log2C = ilog2(C);
