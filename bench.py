@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512", "adjoint512"],
+    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512", "adjoint512", "paper1d"],
                     default="grid1024")
     ap.add_argument("--loop-instances", type=int, default=28,
                     help="sweep512: instances timed one plan at a time for the per-instance loop")
@@ -460,6 +460,59 @@ def run_adjoint(args):
     plan.close()
 
 
+def run_paper1d(args):
+    """The paper's two 1D experiments (Sec. 5) on the GPU: the convergence
+    table at T = 8 (2K points, K = 4 .. 2048) against the scheme on 2 x 8192
+    points (a line that long runs brute force), and the throughput
+    of the time-dependent-V run (hjlo_run_tv, one row of V per step) on
+    2 x 4096 points, timed with CUDA events like the other workloads."""
+    import torch
+    from paper_1210_4090_gb300 import experiments as E, hjlo
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    conv = {}
+    for law in ("pendulum", "tdep"):
+        r = E.convergence(law, [2 ** k for k in range(2, 12)], 2 ** 13)
+        conv[law] = {"order": r["order"], "K_ref": r["K_ref"],
+                     "errors": [[row["K"], row["error"]] for row in r["rows"]]}
+    p = WL.tdep(4096)
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W)
+    dev = torch.device("cuda", local)
+    u0 = torch.tensor(p.u0, device=dev)
+    V = torch.tensor(p.V, device=dev)
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        u.copy_(u0)
+        plan.run_tv(u, V, p.nsteps)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        u.copy_(u0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run_tv(u, V, p.nsteps)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    cnt = plan.sync()
+    plan.close()
+    updates = p.npts * p.nsteps
+    line = {"metric": METRIC + " (1D, time-dependent V)", "value": updates / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (deterministic: the paper's Sec. 5 laws)",
+            "config": {"workload": "tdep", "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
+                       "h": p.h, "P": list(p.P), "T": p.extra["T"],
+                       "note": "one line per launch: latency-bound, not a roofline case"},
+            "convergence": conv, "counters": cnt}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -590,6 +643,8 @@ def main():
         run_sweep(args)
     elif args.workload == "adjoint512":
         run_adjoint(args)
+    elif args.workload == "paper1d":
+        run_paper1d(args)
     else:
         run_ours(args)
 

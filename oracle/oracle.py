@@ -205,3 +205,57 @@ def hbar_estimate(u0, un, nsteps: int, h: float):
     (-mean, -max, -min) of (u^n - u^0)/(n h) over the grid."""
     r = (np.asarray(un, dtype=np.float64) - np.asarray(u0, dtype=np.float64)) / (nsteps * h)
     return float(-r.mean()), float(-r.max()), float(-r.min())
+
+
+def step_matrix(shape, dx, h, P, W, V=None) -> np.ndarray:
+    """One time step as a (min,plus) matrix B (Remark after Prop. prop:klm):
+    u^{n+1}(x) = min_y u^n(y) + B[y, x] with B[y, x] = sum_a k_a[d_a] - h V(x),
+    d_a the displacement in axis a's window with d_a = x_a - y_a (mod N_a), and
+    +inf where no displacement of the window reaches.  Row-major flat indices.
+    The entries are sums in a different order from the scheme's passes, so the
+    matrix product agrees with the scheme up to rounding."""
+    shape = tuple(int(s) for s in np.atleast_1d(shape))
+    ndim = len(shape)
+    dxv, Pv, Wv = _vec(dx, ndim, np.float64), _vec(P, ndim, np.float64), _vec(W, ndim, np.int64)
+    B = np.zeros([1] * (2 * ndim))
+    for a, N in enumerate(shape):
+        dlo, dhi, k = table(N, float(dxv[a]), float(h), float(Pv[a]), int(Wv[a]))
+        Ka = np.full((N, N), np.inf)
+        for d in range(dlo, dhi + 1):
+            for y in range(N):
+                x = (y + d) % N
+                Ka[y, x] = min(Ka[y, x], k[d - dlo])
+        sh = [1] * (2 * ndim)
+        sh[a], sh[ndim + a] = N, N
+        B = B + Ka.reshape(sh)                       # axes (y_0..y_n, x_0..x_n)
+    npts = int(np.prod(shape))
+    B = B.reshape(npts, npts)
+    if V is not None:
+        hV = float(h) * np.asarray(V, dtype=np.float64).reshape(npts)
+        B = B - hV[None, :]
+    return B
+
+
+def minplus_eigenvalue(B: np.ndarray) -> float:
+    """The (min,plus) eigenvalue of a matrix whose graph y -> x (weight
+    B[y, x]) is strongly connected: its minimum cycle mean, by Karp's theorem
+    (R. M. Karp, 1978), with walks allowed to start at any node:
+    D_k(x) = min weight of a k-edge walk ending at x, and
+    lambda = min_x max_{0 <= k < n} (D_n(x) - D_k(x)) / (n - k).
+    For the step matrix, u^n / n -> lambda (Prop. prop:klm), so the discrete
+    effective Hamiltonian of the readout is -lambda / h."""
+    B = np.asarray(B, dtype=np.float64)
+    n = B.shape[0]
+    D = np.empty((n + 1, n))
+    D[0] = 0.0
+    for k in range(1, n + 1):
+        D[k] = np.min(D[k - 1][:, None] + B, axis=0)
+    best = np.inf
+    for x in range(n):
+        if not np.isfinite(D[n, x]):
+            continue
+        fin = np.isfinite(D[:n, x])
+        ks = np.arange(n)[fin]
+        worst = np.max((D[n, x] - D[ks, x]) / (n - ks))
+        best = min(best, worst)
+    return float(best)

@@ -258,8 +258,14 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         int algo = KALGO_MONGE;
         if (d->algo == HJLO_ALGO_BRUTE) algo = KALGO_BRUTE;
         if (d->algo == HJLO_ALGO_AUTO && (ax.weff < 8 || !(ax.curv > 0))) algo = KALGO_BRUTE;
-        if (algo != KALGO_MONGE) all_monge = false;
         s = shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
+        if (s == HJLO_EUNSUPPORTED && algo == KALGO_MONGE && d->algo == HJLO_ALGO_AUTO) {
+            // a line too long for the monotone search's shared-memory layout:
+            // brute force needs only the line and its argmins on chip
+            algo = KALGO_BRUTE;
+            s = shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
+        }
+        if (algo != KALGO_MONGE) all_monge = false;
         apply_test_knobs(ax);
         if (s == HJLO_OK) s = dmalloc((void **)&ax.d_kr64, sizeof(double) * ax.weff, "cudaMalloc(kernel table)");
         if (s == HJLO_OK) {

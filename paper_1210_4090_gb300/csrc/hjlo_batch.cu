@@ -282,6 +282,11 @@ hjlo_status hjlo_batch_create(const hjlo_desc *descs, int32_t count, void *cuda_
         for (int a = 0; a < b->ndim && s == HJLO_OK; ++a) {
             AxisPlan ax = b->inst[(size_t)rep * b->ndim + a];
             s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size());
+            if (s == HJLO_EUNSUPPORTED && ax.algo == KALGO_MONGE && b->descs[rep].algo == HJLO_ALGO_AUTO) {
+                // lines too long for the monotone search's shared memory
+                ax.algo = KALGO_BRUTE;
+                s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size());
+            }
             if (s != HJLO_OK) break;
             // copy the shape onto every member (their tables/offsets stay their own)
             for (int i : g.members) {

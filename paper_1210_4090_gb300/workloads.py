@@ -30,6 +30,14 @@ Hamiltonian H = 1/2|p+P|^2 + V, eq. HPV):
             {cos,sin}(2 pi k2 y), k1,k2 in 1..4, initial values
             ~ N(0, 0.25/|k|^2); u0 = 0; checkpoint every 100 steps.          seed 5
 
+  pendulum  the paper's Sec. 5.1 experiment: 1D on (0, 2 pi], 2K points
+            x_i = (i+1) pi/K, P = 0, V = 1 - cos x, u0 = cos x, T = 8, time
+            step tau = sqrt(dx) rounded down so that an integer number of
+            steps ends at T.  Deterministic.
+  tdep      the paper's Sec. 5.2 experiment: as pendulum with P = 1 and the
+            time-dependent V(t, x) = cos(2x) sin(t), read at t_n = n tau for
+            the step n -> n+1 (one row of V per step).  Deterministic.
+
 Every builder takes optional overrides (grid size, steps) so the same laws
 give small cases for tests.
 """
@@ -40,7 +48,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Problem", "line256", "grid1024", "cube256", "sweep512", "adjoint512",
-           "adjoint_basis", "trig_field", "WORKLOADS"]
+           "adjoint_basis", "trig_field", "pendulum", "tdep", "WORKLOADS"]
 
 
 @dataclass
@@ -54,8 +62,13 @@ class Problem:
     W: tuple                      # per axis; 0 = full periodic window
     nsteps: int
     u0: np.ndarray                # float64, shape `shape`
-    V: np.ndarray | None          # float64, shape `shape` (time-independent)
+    V: np.ndarray | None          # float64, shape `shape` (time-independent), or
+                                  # (nsteps, *shape) when extra["V_per_step"]
     extra: dict = field(default_factory=dict)
+
+    @property
+    def V_per_step(self) -> bool:
+        return bool(self.extra.get("V_per_step", False))
 
     @property
     def npts(self) -> int:
@@ -181,6 +194,36 @@ def adjoint512(N: int = 512, nsteps: int = 2000, W: int = 32, seed: int = 5) -> 
     return Problem("adjoint512", (N, N), (1.0 / N,) * 2, 0.02, (0.3, 0.1), (W, W), nsteps,
                    np.zeros((N, N)), np.ascontiguousarray(V),
                    extra={"coef": coef, "checkpoint_every": 100})
+
+
+def _paper_1d(name: str, K: int, T: float, speed: float, P: float, nsteps: int | None):
+    """Common grid of the two 1D experiments (Sec. 5): 2K points on (0, 2 pi],
+    dx = pi/K, tau <= sqrt(dx) with n tau = T exactly, and a window of
+    displacements wide enough for velocities up to `speed` (W = 0, the full
+    periodic window, when that covers the torus)."""
+    N = 2 * int(K)
+    dx = np.pi / K
+    n = int(np.ceil(T / np.sqrt(dx) - 1e-12)) if nsteps is None else int(nsteps)
+    tau = T / n
+    W = int(np.ceil(speed * tau / dx)) + 1
+    if 2 * W + 1 >= N:
+        W = 0
+    x = (np.arange(N) + 1.0) * dx
+    return N, dx, tau, n, W, x
+
+
+def pendulum(K: int = 4096, T: float = 8.0, speed: float = 4.0, nsteps: int | None = None) -> Problem:
+    N, dx, tau, n, W, x = _paper_1d("pendulum", K, T, speed, 0.0, nsteps)
+    return Problem("pendulum", (N,), (dx,), tau, (0.0,), (W,), n, np.cos(x), 1.0 - np.cos(x),
+                   extra={"K": K, "T": tau * n, "x": x})
+
+
+def tdep(K: int = 4096, T: float = 8.0, speed: float = 4.0, nsteps: int | None = None) -> Problem:
+    N, dx, tau, n, W, x = _paper_1d("tdep", K, T, speed, 1.0, nsteps)
+    t = np.arange(n) * tau
+    V = np.sin(t)[:, None] * np.cos(2.0 * x)[None, :]
+    return Problem("tdep", (N,), (dx,), tau, (1.0,), (W,), n, np.cos(x), np.ascontiguousarray(V),
+                   extra={"K": K, "T": tau * n, "x": x, "V_per_step": True})
 
 
 WORKLOADS = {"line256": line256, "grid1024": grid1024, "cube256": cube256,
