@@ -259,3 +259,140 @@ def minplus_eigenvalue(B: np.ndarray) -> float:
         worst = np.max((D[n, x] - D[ks, x]) / (n - ks))
         best = min(best, worst)
     return float(best)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own fast (min,plus)-convolution (Sec. 4): decompose the source
+# line into convex and concave components, convolve each with the convex
+# kernel in linear time, take the minimum.  Plain Python loops (small cases).
+# Every output value is one candidate u(y) + k(d), as in the scheme, so the
+# result is never below the scheme's and equals it wherever the kept
+# candidates include a minimiser (always, in exact arithmetic, at eta = 0).
+
+def convex_convex(f, g):
+    """f on [0, n] and g on [0, m] convex (Theorem th:convex, Algorithm 1):
+    the pieces of f and g put end to end by increasing slope -- f's piece
+    first when its slope is strictly smaller, as in Algorithm 1.  The vertex
+    after i pieces of f and j of g has the value f(i) + g(j) (the telescoped
+    running sum of Algorithm 1).  Returns h on [0, n + m]."""
+    n, m = len(f) - 1, len(g) - 1
+    h = np.empty(n + m + 1)
+    i = j = 0
+    h[0] = f[0] + g[0]
+    while i + j < n + m:
+        if i < n and (j == m or (f[i + 1] - f[i]) < (g[j + 1] - g[j])):
+            i += 1
+        else:
+            j += 1
+        h[i + j] = f[i] + g[j]
+    return h
+
+
+def convex_concave(f, g):
+    """f on [0, n] convex, g on [0, m] concave, m >= 1 (Lemmas lm:seg and
+    lm:simplif, Theorem th:ccc; Algorithm 2 walks the same three parts).
+    With rho_j = g(j+1) - g(j) and alpha_j the first vertex of f whose next
+    slope f(i+1) - f(i) is >= rho_j (n if none):
+      (i)   f(x) + g(0)            for x in [0, alpha_0]          (first convex part)
+      (ii)  f(alpha_j) + g(j), f(alpha_j) + g(j+1)
+                                   at x = j + alpha_j, j + 1 + alpha_j  (concave part)
+      (iii) f(x - m) + g(m)        for x in [m + alpha_{m-1}, m + n]  (last convex part)
+    and h is their pointwise minimum on [0, n + m]."""
+    n, m = len(f) - 1, len(g) - 1
+    h = np.full(n + m + 1, np.inf)
+
+    def alpha(rho):
+        for i in range(n):
+            if f[i + 1] - f[i] >= rho:
+                return i
+        return n
+
+    a0 = alpha(g[1] - g[0])
+    for x in range(a0 + 1):
+        h[x] = min(h[x], f[x] + g[0])
+    for j in range(m):
+        a = alpha(g[j + 1] - g[j])
+        h[j + a] = min(h[j + a], f[a] + g[j])
+        h[j + 1 + a] = min(h[j + 1 + a], f[a] + g[j + 1])
+        if j == m - 1:
+            for x in range(m + a, m + n + 1):
+                h[x] = min(h[x], f[x - m] + g[m])
+    return h
+
+
+def decompose(g, eta: float = 0.0):
+    """Split g[0..L-1] into consecutive components sharing their end points
+    (Sec. 4.3 step 1, with the tolerance of Sec. 4.4): the first slope
+    increment of a component fixes its kind -- convex when it is >= -eta,
+    concave otherwise -- and the component is extended while the following
+    increments keep the kind (convex: >= -eta; concave: <= 0).  Returns
+    [(start, end, convex)]; a single point is one convex component."""
+    L = len(g)
+    if L == 1:
+        return [(0, 0, True)]
+    rho = [g[p + 1] - g[p] for p in range(L - 1)]
+    out = []
+    s = 0
+    while s < L - 1:
+        e = s + 1
+        if e == L - 1:
+            out.append((s, e, True))
+            break
+        convex = (rho[s + 1] - rho[s]) >= -eta
+        while e + 1 <= L - 1:
+            inc = rho[e] - rho[e - 1]
+            if not (inc >= -eta if convex else inc <= 0.0):
+                break
+            e += 1
+        out.append((s, e, convex))
+        s = e
+    return out
+
+
+def decomp_line(src, k, eta: float = 0.0):
+    """One line of an axis pass by the decomposition method (Sec. 4.3).
+    k[i] = k_a[dlo + i] for i in [0, n] (n = dhi - dlo) is the convex kernel;
+    src[y'] = u((y' - dhi) mod N) for y' in [0, N + n) is the lifted source
+    line, so that output x in [0, N) is the minimum over i of
+    src[x + n - i] + k[i], i.e. entry x + n of the (min,plus) convolution of
+    src and k.  Returns (the N outputs, the number of components)."""
+    n = len(k) - 1
+    L = len(src)
+    N = L - n
+    comps = decompose(src, eta)
+    h = np.full(L + n, np.inf)
+    for s, e, convex in comps:
+        g = src[s:e + 1]
+        part = convex_convex(k, g) if (convex or e == s) else convex_concave(k, g)
+        h[s:s + len(part)] = np.minimum(h[s:s + len(part)], part)
+    return h[n:n + N], len(comps)
+
+
+def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_per_step: bool = False):
+    """nsteps of the scheme with every axis pass computed by the decomposition
+    method (axis 0 first, then fl(m - fl(h V)) as in the scheme).  Returns
+    (u, total number of components over all lines and passes)."""
+    u = np.array(u0, dtype=np.float64, copy=True)
+    shape = u.shape
+    ndim = u.ndim
+    dxv, Pv, Wv = _vec(dx, ndim, np.float64), _vec(P, ndim, np.float64), _vec(W, ndim, np.int64)
+    tabs = [table(shape[a], float(dxv[a]), float(h), float(Pv[a]), int(Wv[a])) for a in range(ndim)]
+    ncomp = 0
+    for step in range(nsteps):
+        for a in range(ndim):
+            dlo, dhi, k = tabs[a]
+            N = shape[a]
+            n = dhi - dlo
+            v = np.moveaxis(u, a, -1)
+            out = np.empty_like(v)
+            for idx in np.ndindex(*v.shape[:-1]):
+                line = v[idx]
+                src = line[(np.arange(N + n) - dhi) % N]
+                out[idx], c = decomp_line(src, k, eta)
+                ncomp += c
+            u = np.ascontiguousarray(np.moveaxis(out, -1, a))
+        if V is not None:
+            Vs = np.asarray(V, dtype=np.float64)
+            Vn = Vs[step] if V_per_step else Vs
+            u = u - float(h) * Vn
+    return u, ncomp
