@@ -67,7 +67,9 @@ typedef enum {
 typedef enum {
     HJLO_ALGO_AUTO = 0,     /* library's choice (results do not depend on it) */
     HJLO_ALGO_BRUTE = 1,    /* every window candidate evaluated in binary64 */
-    HJLO_ALGO_MONGE = 2     /* monotone-argmin search (see hjlo_plan_create) */
+    HJLO_ALGO_MONGE = 2,    /* monotone-argmin search (see hjlo_plan_create) */
+    HJLO_ALGO_DECOMP = 3    /* the paper's own fast convolution (Sec. 4): convex/concave
+                               decomposition of every line; see hjlo_plan_set_tolerance */
 } hjlo_algo;
 
 /* Problem descriptor (one grid).  Sec. 2.3 eq. cost2 / eqconvol, Sec. 3.3. */
@@ -104,6 +106,7 @@ typedef struct {
     int64_t steps;                /* time steps enqueued on this plan so far */
     int32_t error_flags;          /* bit 0: precondition, bit 1: wait timeout */
     int32_t reserved;
+    int64_t components;           /* HJLO_ALGO_DECOMP: convex/concave components convolved */
 } hjlo_counters;
 
 /*
@@ -116,9 +119,20 @@ typedef struct {
  * searched in a narrow range bracketed by its neighbours' argmins.  The plan
  * checks that the table's second differences are positive; each launch
  * re-checks the rounding margin per line and falls back to brute force for a
- * line that fails it (counted in hjlo_counters).
+ * line that fails it (counted in hjlo_counters).  Under HJLO_ALGO_AUTO a line
+ * too long for the monotone search's shared-memory layout takes brute force.
+ * HJLO_ALGO_DECOMP runs every pass by the paper's own method (Sec. 4): each
+ * line is cut into convex and concave components (tolerance eta, Sec. 4.4,
+ * default 0), each is convolved with the convex kernel in linear time
+ * (Theorem th:convex, Algorithm 1; Lemmas lm:seg, lm:simplif, Theorem th:ccc,
+ * Algorithm 2) and the minimum over components is taken.  Its outputs are
+ * candidates of the scheme (never below it; equal to it in exact arithmetic
+ * at eta = 0).  It needs binary64 storage, a strictly convex table
+ * (HJLO_EPRECOND otherwise) and records no argmins (hjlo_step with
+ * argmin_out and hjlo_adjoint return HJLO_EUNSUPPORTED).
  * Errors: HJLO_EINVAL (bad descriptor), HJLO_EUNSUPPORTED (a line of the grid
- * does not fit in one CTA's shared memory), HJLO_ENOMEM, HJLO_ECUDA.
+ * does not fit in one CTA's shared memory), HJLO_EPRECOND, HJLO_ENOMEM,
+ * HJLO_ECUDA.
  */
 hjlo_status hjlo_plan_create(const hjlo_desc *desc, void *cuda_stream, hjlo_plan **out);
 
@@ -128,6 +142,16 @@ hjlo_status hjlo_plan_destroy(hjlo_plan *plan);
 
 /* Copy the resolved windows and table facts into *info (host). */
 hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
+
+/*
+ * Convexity tolerance eta >= 0 of an HJLO_ALGO_DECOMP plan (Sec. 4.4): a
+ * component stays "convex" while its slope increments are >= -eta, so nearly
+ * affine stretches join fewer, longer components (fewer components, larger
+ * values where the stretch is not convex).  Waits for the plan's stream;
+ * later steps use the new value.  Errors: HJLO_EINVAL (another algorithm,
+ * eta negative or not finite).
+ */
+hjlo_status hjlo_plan_set_tolerance(hjlo_plan *plan, double eta);
 
 /*
  * One time step (eq. eqconvol): u_out = T(u_in).  u_in and u_out hold npts

@@ -306,6 +306,8 @@ hjlo_status hjlo_adjoint(hjlo_plan *p, const double *u0, const double *V, int64_
 {
     if (!p) return set_error(HJLO_EINVAL, "plan is NULL");
     if (p->dtype != HJLO_F64) return set_error(HJLO_EUNSUPPORTED, "the adjoint needs a binary64 plan");
+    if (p->algo == HJLO_ALGO_DECOMP)
+        return set_error(HJLO_EUNSUPPORTED, "the adjoint follows argmins, which the decomposition method does not record");
     if (!u0 || !ubar_n || !ubar_0) return set_error(HJLO_EINVAL, "u0, ubar_n and ubar_0 are required");
     if (nsteps < 0) return set_error(HJLO_EINVAL, "nsteps must be >= 0");
     hjlo_status s = plan_set_device(p);

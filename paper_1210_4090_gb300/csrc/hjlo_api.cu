@@ -218,7 +218,9 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
     if (!d) return set_error(HJLO_EINVAL, "descriptor is NULL");
     if (d->ndim < 1 || d->ndim > HJLO_MAX_DIM) return set_error(HJLO_EINVAL, "ndim must be 1..3");
     if (d->dtype != HJLO_F64 && d->dtype != HJLO_F32_STORAGE) return set_error(HJLO_EINVAL, "unknown dtype");
-    if (d->algo < HJLO_ALGO_AUTO || d->algo > HJLO_ALGO_MONGE) return set_error(HJLO_EINVAL, "unknown algo");
+    if (d->algo < HJLO_ALGO_AUTO || d->algo > HJLO_ALGO_DECOMP) return set_error(HJLO_EINVAL, "unknown algo");
+    if (d->algo == HJLO_ALGO_DECOMP && d->dtype != HJLO_F64)
+        return set_error(HJLO_EUNSUPPORTED, "the decomposition method runs in binary64 storage only");
     if (d->reserved != 0) return set_error(HJLO_EINVAL, "reserved field must be 0");
     if (!(d->h > 0) || !std::isfinite(d->h)) return set_error(HJLO_EINVAL, "h must be finite and > 0");
     long long npts = 1;
@@ -258,7 +260,9 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         int algo = KALGO_MONGE;
         if (d->algo == HJLO_ALGO_BRUTE) algo = KALGO_BRUTE;
         if (d->algo == HJLO_ALGO_AUTO && (ax.weff < 8 || !(ax.curv > 0))) algo = KALGO_BRUTE;
-        s = shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
+        if (d->algo == HJLO_ALGO_DECOMP) algo = KALGO_DECOMP;
+        s = (algo == KALGO_DECOMP) ? shape_decomp(ax, df.smem_optin)
+                                   : shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
         if (s == HJLO_EUNSUPPORTED && algo == KALGO_MONGE && d->algo == HJLO_ALGO_AUTO) {
             // a line too long for the monotone search's shared-memory layout:
             // brute force needs only the line and its argmins on chip
@@ -275,7 +279,7 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         free(k64);
         if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
     }
-    p->algo = all_monge ? HJLO_ALGO_MONGE : HJLO_ALGO_BRUTE;
+    p->algo = (d->algo == HJLO_ALGO_DECOMP) ? HJLO_ALGO_DECOMP : (all_monge ? HJLO_ALGO_MONGE : HJLO_ALGO_BRUTE);
     s = dmalloc((void **)&p->d_counters, sizeof(unsigned long long) * CNT_N, "cudaMalloc(counters)");
     if (s == HJLO_OK) s = dmalloc((void **)&p->d_flags, sizeof(int), "cudaMalloc(flags)");
     if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
@@ -423,6 +427,22 @@ hjlo_status hjlo_hbar(hjlo_plan *p, const void *u0, const void *un, int64_t nste
     return HJLO_OK;
 }
 
+hjlo_status hjlo_plan_set_tolerance(hjlo_plan *p, double eta)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (p->algo != HJLO_ALGO_DECOMP) return set_error(HJLO_EINVAL, "the tolerance applies to HJLO_ALGO_DECOMP plans");
+    if (!(eta >= 0.0) || !std::isfinite(eta)) return set_error(HJLO_EINVAL, "eta must be finite and >= 0");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    // launches already enqueued keep their own copy of the parameters; the
+    // cached graph holds the old value and is rebuilt on next use
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    for (int a = 0; a < p->ndim; ++a) p->ax[a].eta = eta;
+    destroy_graph(p);
+    return HJLO_OK;
+}
+
 hjlo_status hjlo_sync(hjlo_plan *p, hjlo_counters *out)
 {
     hjlo_status s = check_plan(p);
@@ -439,6 +459,7 @@ hjlo_status hjlo_sync(hjlo_plan *p, hjlo_counters *out)
         memset(out, 0, sizeof(*out));
         out->exact_rescans = (int64_t)c[CNT_RESCAN];
         out->brute_fallback_lines = (int64_t)c[CNT_FALLBACK];
+        out->components = (int64_t)c[CNT_COMPONENTS];
         out->steps = p->steps;
         out->error_flags = flags;
     }

@@ -1,0 +1,282 @@
+// hjlo_decomp.cu -- the paper's own fast (min,plus) convolution (Sec. 4) as
+// an axis pass: every line is split into convex and concave components
+// (Sec. 4.3, with the tolerance eta of Sec. 4.4), each component is
+// convolved with the convex kernel in linear time (Theorem th:convex /
+// Algorithm 1 for a convex component; the three parts of Lemmas lm:seg and
+// lm:simplif / Theorem th:ccc / Algorithm 2 for a concave one), and the
+// output is the minimum over components (Sec. 4.3 step 3).
+//
+// One CTA per line.  The lifted source line and the kernel are staged in
+// shared memory; the slope-increment kinds of all interior points are
+// classified in parallel into two bitmaps; one thread walks the bitmaps to
+// cut the components greedily (the cut is a left-to-right dependency chain,
+// a few word operations per component); then the threads take whole
+// components and merge their outputs into per-output order-preserving keys
+// with shared-memory atomicMin, so the result does not depend on the order
+// in which components finish.  Every output value is one candidate
+// fl(u(y) + k(d)) of the scheme, so the pass is never below the scheme's.
+#include "hjlo_internal.h"
+
+namespace hjlo {
+
+namespace {
+
+constexpr int kDecompThreads = 256;
+constexpr unsigned kConvexBit = 0x80000000u;
+
+struct DecompParams {
+    const double *src;
+    double *dst;
+    const double *hv;
+    double hscale;
+    int hv_scaled;
+    const double *kr64;          // kr64[t] = k[dhi - t]; f(i) = k[dlo + i] = kr64[n - i]
+    unsigned long long *counters;
+    int *flags;
+    long long N, inner, outer;
+    int n;                       // window length - 1
+    int hoff;                    // (-dhi) mod N
+    int L;                       // N + n source points
+    int nwords;                  // (L + 31) / 32
+    double eta;
+    int off_f, off_keys, off_cv, off_cc, off_comp, off_misc;
+};
+
+__device__ __forceinline__ void emit(unsigned long long *keys, int n, int N, int z, double v)
+{
+    const int x = z - n;
+    if (x >= 0 && x < N) atomicMin(&keys[x], dkey(v));
+}
+
+// First point q in [from, to] whose bit is clear, or `none`.
+__device__ int next_clear(const unsigned *bits, int from, int to, int none)
+{
+    if (from > to) return none;
+    int w = from >> 5;
+    unsigned word = ~bits[w] & (0xffffffffu << (from & 31));
+    const int wlast = to >> 5;
+    for (;;) {
+        if (w == wlast) word &= (to & 31) == 31 ? 0xffffffffu : ((1u << ((to & 31) + 1)) - 1u);
+        if (word) return (w << 5) + __ffs(word) - 1;
+        if (++w > wlast) return none;
+        word = ~bits[w];
+    }
+}
+
+// Algorithm 1 on f[0..n] and g[0..m]: vertex after i pieces of f and j of g
+// is f(i) + g(j); f's piece goes first when its slope is strictly smaller.
+__device__ void conv_convex(const double *f, int n, const double *g, int m, int s, unsigned long long *keys,
+                            int N)
+{
+    int i = 0, j = 0;
+    emit(keys, n, N, s, __dadd_rn(f[0], g[0]));
+    while (i + j < n + m) {
+        if (i < n && (j == m || __dsub_rn(f[i + 1], f[i]) < __dsub_rn(g[j + 1], g[j])))
+            ++i;
+        else
+            ++j;
+        emit(keys, n, N, s + i + j, __dadd_rn(f[i], g[j]));
+    }
+}
+
+// Convex f[0..n] by concave g[0..m], m >= 1: the first convex part, the
+// segments of g translated by alpha_j (the first vertex of f whose next slope
+// is >= rho_j; it only moves down as the slopes of g decrease), the last
+// convex part.
+__device__ void conv_concave(const double *f, int n, const double *g, int m, int s, unsigned long long *keys,
+                             int N)
+{
+    double rho = __dsub_rn(g[1], g[0]);
+    int a = 0;
+    while (a < n && !(__dsub_rn(f[a + 1], f[a]) >= rho)) ++a;
+    for (int x = 0; x <= a; ++x) emit(keys, n, N, s + x, __dadd_rn(f[x], g[0]));
+    for (int j = 0; j < m; ++j) {
+        if (j > 0) {
+            rho = __dsub_rn(g[j + 1], g[j]);
+            while (a > 0 && __dsub_rn(f[a], f[a - 1]) >= rho) --a;
+        }
+        emit(keys, n, N, s + j + a, __dadd_rn(f[a], g[j]));
+        emit(keys, n, N, s + j + 1 + a, __dadd_rn(f[a], g[j + 1]));
+    }
+    for (int x = m + a; x <= m + n; ++x) emit(keys, n, N, s + x, __dadd_rn(f[x - m], g[m]));
+}
+
+__global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *g = reinterpret_cast<double *>(smem);
+    double *f = reinterpret_cast<double *>(smem + p.off_f);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem + p.off_keys);
+    unsigned *cv = reinterpret_cast<unsigned *>(smem + p.off_cv);
+    unsigned *cc = reinterpret_cast<unsigned *>(smem + p.off_cc);
+    unsigned *comp = reinterpret_cast<unsigned *>(smem + p.off_comp);
+    int *misc = reinterpret_cast<int *>(smem + p.off_misc);
+
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+    const long long line = blockIdx.x;
+    const long long o = line / p.inner, in = line - o * p.inner;
+    const long long base = o * p.N * p.inner + in, stride = p.inner;
+    const int N = (int)p.N, n = p.n, L = p.L;
+
+    // ---- stage: g[y] = u((y - dhi) mod N), f(i) = k[dlo + i]
+    for (int y = tid; y < L; y += nthr) g[y] = p.src[base + (long long)((y + p.hoff) % N) * stride];
+    for (int i = tid; i <= n; i += nthr) f[i] = p.kr64[n - i];
+    for (int x = tid; x < N; x += nthr) keys[x] = ~0ull;
+    __syncthreads();
+
+    // ---- kinds of the slope increment at every interior point q:
+    // convex rule (increment >= -eta) and concave rule (increment <= 0)
+    for (int b0 = (tid >> 5) << 5; b0 < (p.nwords << 5); b0 += nthr) {
+        const int q = b0 + lane;
+        bool okv = false, okc = false;
+        if (q >= 1 && q <= L - 2) {
+            const double inc = __dsub_rn(__dsub_rn(g[q + 1], g[q]), __dsub_rn(g[q], g[q - 1]));
+            okv = inc >= -p.eta;
+            okc = inc <= 0.0;
+        }
+        const unsigned wv = __ballot_sync(0xffffffffu, okv);
+        const unsigned wc = __ballot_sync(0xffffffffu, okc);
+        if (lane == 0) {
+            cv[b0 >> 5] = wv;
+            cc[b0 >> 5] = wc;
+        }
+    }
+    __syncthreads();
+
+    // ---- greedy cut: a component starting at s takes the kind of the
+    // increment at s + 1 and ends at the first later point that breaks it
+    if (tid == 0) {
+        int nc = 0;
+        if (L == 1) {
+            comp[nc++] = 0u | kConvexBit;
+            comp[nc] = 0u;
+        } else {
+            int s = 0;
+            while (s < L - 1) {
+                bool convex = true;
+                int e = L - 1;
+                if (s + 1 < L - 1) {
+                    convex = (cv[(s + 1) >> 5] >> ((s + 1) & 31)) & 1u;
+                    e = next_clear(convex ? cv : cc, s + 2, L - 2, L - 1);
+                }
+                comp[nc++] = (unsigned)s | (convex ? kConvexBit : 0u);
+                s = e;
+            }
+            comp[nc] = (unsigned)(L - 1);
+        }
+        misc[0] = nc;
+        atomicAdd(&p.counters[CNT_COMPONENTS], (unsigned long long)nc);
+    }
+    __syncthreads();
+
+    // ---- convolve the components, minimum into the keys
+    const int nc = misc[0];
+    for (int c = tid; c < nc; c += nthr) {
+        const int s = (int)(comp[c] & ~kConvexBit);
+        const bool convex = (comp[c] & kConvexBit) != 0;
+        const int e = (int)(comp[c + 1] & ~kConvexBit);
+        const int m = e - s;
+        if (convex || m == 0)
+            conv_convex(f, n, g + s, m, s, keys, N);
+        else
+            conv_concave(f, n, g + s, m, s, keys, N);
+    }
+    __syncthreads();
+
+    // ---- values, potential term, stores
+    for (int x = tid; x < N; x += nthr) {
+        const unsigned long long k = keys[x];
+        if (k == ~0ull) {                  // no component reached x: cannot happen for a convex kernel
+            atomicOr(p.flags, FLAG_PRECOND);
+            continue;
+        }
+        double m = dkey_decode(k);
+        const long long at = base + (long long)x * stride;
+        if (p.hv) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, p.hv[at]) : p.hv[at]);
+        p.dst[at] = m;
+    }
+}
+
+size_t decomp_smem(const AxisPlan &ax, DecompParams *p)
+{
+    const long long N = ax.N, n = ax.weff - 1, L = N + n, nwords = (L + 31) / 32;
+    size_t off = 0;
+    off += sizeof(double) * L;                                  // g
+    const size_t off_f = off;
+    off += sizeof(double) * (n + 1);
+    off = (off + 15) & ~size_t(15);
+    const size_t off_keys = off;
+    off += sizeof(unsigned long long) * N;
+    const size_t off_cv = off;
+    off += sizeof(unsigned) * nwords;
+    const size_t off_cc = off;
+    off += sizeof(unsigned) * nwords;
+    const size_t off_comp = off;
+    off += sizeof(unsigned) * (L + 1);
+    const size_t off_misc = off;
+    off += 16;
+    if (p) {
+        p->off_f = (int)off_f;
+        p->off_keys = (int)off_keys;
+        p->off_cv = (int)off_cv;
+        p->off_cc = (int)off_cc;
+        p->off_comp = (int)off_comp;
+        p->off_misc = (int)off_misc;
+        p->n = (int)n;
+        p->L = (int)L;
+        p->nwords = (int)nwords;
+    }
+    return off;
+}
+
+}  // namespace
+
+hjlo_status decomp_allow_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(decomp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return e == cudaSuccess ? HJLO_OK : cuda_error(e, "cudaFuncSetAttribute(decomp)");
+}
+
+hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin)
+{
+    ax.algo = KALGO_DECOMP;
+    ax.layout = (ax.inner == 1) ? LAYOUT_CONTIG : LAYOUT_STRIDED;
+    ax.smem = decomp_smem(ax, nullptr);
+    if (ax.smem > smem_optin || ax.N + ax.weff > (1LL << 30))
+        return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit the decomposition pass", ax.N);
+    if (ax.weff >= 3 && !(ax.curv > 0))
+        return set_error(HJLO_EPRECOND, "the decomposition pass needs a strictly convex kernel table");
+    ax.threads = kDecompThreads;
+    ax.ntiles = ax.inner * ax.outer;
+    if (ax.ntiles > 0x7fffffffLL) return set_error(HJLO_EUNSUPPORTED, "too many lines");
+    ax.C = 1;
+    ax.log2C = 0;
+    return HJLO_OK;
+}
+
+hjlo_status launch_decomp(const AxisPlan &ax, const void *src, void *dst, const double *hv, double hv_scale,
+                          unsigned long long *counters, int *flags, cudaStream_t st)
+{
+    DecompParams p;
+    memset(&p, 0, sizeof(p));
+    decomp_smem(ax, &p);
+    p.src = reinterpret_cast<const double *>(src);
+    p.dst = reinterpret_cast<double *>(dst);
+    p.hv = hv;
+    p.hscale = hv_scale;
+    p.hv_scaled = (hv_scale != 0.0) ? 1 : 0;
+    p.kr64 = ax.d_kr64;
+    p.counters = counters;
+    p.flags = flags;
+    p.N = ax.N;
+    p.inner = ax.inner;
+    p.outer = ax.outer;
+    p.hoff = ax.hoff;
+    p.eta = ax.eta;
+    decomp_kernel<<<(unsigned)ax.ntiles, ax.threads, ax.smem, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "decomposition kernel launch");
+    return HJLO_OK;
+}
+
+}  // namespace hjlo

@@ -45,9 +45,9 @@
 namespace hjlo {
 
 enum { LAYOUT_CONTIG = 0, LAYOUT_STRIDED = 1 };
-enum { KALGO_BRUTE = 1, KALGO_MONGE = 2 };
+enum { KALGO_BRUTE = 1, KALGO_MONGE = 2, KALGO_DECOMP = 3 };
 enum { FLAG_PRECOND = 1, FLAG_TIMEOUT = 2 };
-enum { CNT_RESCAN = 0, CNT_FALLBACK = 1, CNT_N = 4 };
+enum { CNT_RESCAN = 0, CNT_FALLBACK = 1, CNT_COMPONENTS = 2, CNT_N = 4 };
 
 struct PassParams {
     const void *src;          // tile source (global)

@@ -28,6 +28,7 @@ struct AxisPlan {
     long long wait_ns = 500000000LL;       // first TMA wait bound (0.5 s)
     int test_extra_tx = 0;                 // test knob, see apply_test_knobs
     int wide_mul = 2, wide_add = 8;        // warp offload of wide brackets (see PassParams)
+    double eta = 0.0;                      // DECOMP: convexity tolerance of the decomposition
     int by = 1, nbox = 1, lp = 0;
     long long ntiles = 0, tiles_per_outer = 1;
     size_t smem = 0;
@@ -90,6 +91,12 @@ hjlo_status kern_allow_smem_f32_strided();
 hjlo_status kern_single_f32_strided(const AxisPlan &ax, const CUtensorMap &map, const PassParams &p, cudaStream_t st);
 hjlo_status kern_batch_f32_strided(const AxisPlan &ax, const BatchItem *items, const PassParams &p, long long count,
                              cudaStream_t st);
+
+// The paper's decomposition method as an axis pass (hjlo_decomp.cu).
+hjlo_status decomp_allow_smem();
+hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin);
+hjlo_status launch_decomp(const AxisPlan &ax, const void *src, void *dst, const double *hv, double hv_scale,
+                          unsigned long long *counters, int *flags, cudaStream_t st);
 
 // One-time per-device kernel attributes; call outside stream capture.
 hjlo_status prepare_kernels();

@@ -133,6 +133,7 @@ extern "C" hjlo_status hjlo_step_noalloc(const hjlo_desc *d, void *cuda_stream, 
     if (!u_in || !u_out) return set_error(HJLO_EINVAL, "u_in/u_out is NULL");
     if (d->ndim < 1 || d->ndim > HJLO_MAX_DIM) return set_error(HJLO_EINVAL, "ndim must be 1..3");
     if (d->dtype != HJLO_F64 && d->dtype != HJLO_F32_STORAGE) return set_error(HJLO_EINVAL, "unknown dtype");
+    if (d->algo == HJLO_ALGO_DECOMP) return set_error(HJLO_EUNSUPPORTED, "the no-allocation step runs the brute or monotone pass");
     if (d->algo < HJLO_ALGO_AUTO || d->algo > HJLO_ALGO_MONGE) return set_error(HJLO_EINVAL, "unknown algo");
     if (d->reserved != 0) return set_error(HJLO_EINVAL, "reserved field must be 0");
     if (!(d->h > 0) || !std::isfinite(d->h)) return set_error(HJLO_EINVAL, "h must be finite and > 0");

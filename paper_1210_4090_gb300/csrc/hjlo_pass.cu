@@ -366,6 +366,7 @@ hjlo_status prepare_kernels()
     if ((s = kern_allow_smem_f64_strided()) != HJLO_OK) return s;
     if ((s = kern_allow_smem_f32_contig()) != HJLO_OK) return s;
     if ((s = kern_allow_smem_f32_strided()) != HJLO_OK) return s;
+    if ((s = decomp_allow_smem()) != HJLO_OK) return s;
     encode_fn();
     if (dev < 64) done[dev] = true;
     return HJLO_OK;
@@ -459,6 +460,11 @@ hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *ds
                         double hv_scale, int32_t *amin, unsigned long long *counters, int *flags,
                         cudaStream_t st)
 {
+    if (ax.algo == KALGO_DECOMP) {
+        if (amin) return set_error(HJLO_EUNSUPPORTED, "the decomposition method records no argmins");
+        if (dtype != HJLO_F64) return set_error(HJLO_EUNSUPPORTED, "the decomposition method runs in binary64");
+        return launch_decomp(ax, src, dst, hv, hv_scale, counters, flags, st);
+    }
     const int esize = (dtype == HJLO_F64) ? 8 : 4;
     PassParams p;
     fill_params(ax, p);

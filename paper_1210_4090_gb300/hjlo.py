@@ -19,10 +19,10 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Plan", "Batch", "HjloError", "lib", "library_path", "exported_symbols", "step_noalloc",
-           "F64", "F32_STORAGE", "ALGO_AUTO", "ALGO_BRUTE", "ALGO_MONGE"]
+           "F64", "F32_STORAGE", "ALGO_AUTO", "ALGO_BRUTE", "ALGO_MONGE", "ALGO_DECOMP"]
 
 F64, F32_STORAGE = 0, 1
-ALGO_AUTO, ALGO_BRUTE, ALGO_MONGE = 0, 1, 2
+ALGO_AUTO, ALGO_BRUTE, ALGO_MONGE, ALGO_DECOMP = 0, 1, 2, 3
 _STATUS = {0: "HJLO_OK", 1: "HJLO_EINVAL", 2: "HJLO_ENOMEM", 3: "HJLO_ECUDA", 4: "HJLO_EPRECOND",
            5: "HJLO_ETIMEOUT", 6: "HJLO_EUNSUPPORTED"}
 
@@ -42,7 +42,7 @@ class Facts(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [("exact_rescans", _i64), ("brute_fallback_lines", _i64), ("steps", _i64),
-                ("error_flags", _i32), ("reserved", _i32)]
+                ("error_flags", _i32), ("reserved", _i32), ("components", _i64)]
 
 
 class HjloError(RuntimeError):
@@ -62,6 +62,7 @@ _SIGS = [
     ("hjlo_plan_create", _i32, [ctypes.POINTER(Desc), _vp, ctypes.POINTER(_vp)]),
     ("hjlo_plan_destroy", _i32, [_vp]),
     ("hjlo_plan_info", _i32, [_vp, ctypes.POINTER(Facts)]),
+    ("hjlo_plan_set_tolerance", _i32, [_vp, _f64]),
     ("hjlo_step", _i32, [_vp, _vp, _vp, _vp, _vp]),
     ("hjlo_run", _i32, [_vp, _vp, _vp, _i64]),
     ("hjlo_run_tv", _i32, [_vp, _vp, _vp, _i64]),
@@ -210,11 +211,15 @@ class Plan:
         except Exception:
             pass
 
+    def set_tolerance(self, eta: float):
+        """Convexity tolerance of an ALGO_DECOMP plan (Sec. 4.4)."""
+        _check(lib().hjlo_plan_set_tolerance(self._h, float(eta)), "hjlo_plan_set_tolerance")
+
     def info(self) -> dict:
         f = Facts()
         _check(lib().hjlo_plan_info(self._h, ctypes.byref(f)), "hjlo_plan_info")
         nd = f.ndim
-        return {"algo": {1: "brute", 2: "monge"}.get(f.algo, f.algo), "npts": f.npts,
+        return {"algo": {1: "brute", 2: "monge", 3: "decomp"}.get(f.algo, f.algo), "npts": f.npts,
                 "dlo": list(f.dlo[:nd]), "dhi": list(f.dhi[:nd]), "centre": list(f.centre[:nd]),
                 "kmin": list(f.kmin[:nd]), "curvature": list(f.curvature[:nd])}
 
@@ -290,7 +295,7 @@ class Plan:
         c = Counters()
         st = lib().hjlo_sync(self._h, ctypes.byref(c))
         res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
-               "steps": c.steps, "error_flags": c.error_flags}
+               "steps": c.steps, "error_flags": c.error_flags, "components": c.components}
         _check(st, "hjlo_sync")
         return res
 
