@@ -145,9 +145,10 @@ hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
 
 /*
  * Convexity tolerance eta >= 0 of an HJLO_ALGO_DECOMP plan (Sec. 4.4): a
- * component stays "convex" while its slope increments are >= -eta, so nearly
- * affine stretches join fewer, longer components (fewer components, larger
- * values where the stretch is not convex).  Waits for the plan's stream;
+ * component stays "convex" while the increase of its slopes, taken per unit
+ * length ((u(i+1) - u(i)) / dx_a), is >= -eta (second differences
+ * >= -eta * dx_a), so nearly affine stretches join fewer, longer components
+ * (fewer components, larger values where the stretch is not convex).  Waits for the plan's stream;
  * later steps use the new value.  Errors: HJLO_EINVAL (another algorithm,
  * eta negative or not finite).
  */

@@ -370,8 +370,11 @@ def decomp_line(src, k, eta: float = 0.0):
 
 def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_per_step: bool = False):
     """nsteps of the scheme with every axis pass computed by the decomposition
-    method (axis 0 first, then fl(m - fl(h V)) as in the scheme).  Returns
-    (u, total number of components over all lines and passes)."""
+    method (axis 0 first, then fl(m - fl(h V)) as in the scheme).  eta is the
+    tolerance on the increase of the slopes (u(i+1) - u(i)) / dx along the
+    line, as the slopes of Sec. 4.1 are taken per unit length: on axis a the
+    second differences are compared with -fl(eta * dx_a).  Returns (u, total
+    number of components over all lines and passes)."""
     u = np.array(u0, dtype=np.float64, copy=True)
     shape = u.shape
     ndim = u.ndim
@@ -388,7 +391,7 @@ def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_
             for idx in np.ndindex(*v.shape[:-1]):
                 line = v[idx]
                 src = line[(np.arange(N + n) - dhi) % N]
-                out[idx], c = decomp_line(src, k, eta)
+                out[idx], c = decomp_line(src, k, float(eta) * float(dxv[a]))
                 ncomp += c
             u = np.ascontiguousarray(np.moveaxis(out, -1, a))
         if V is not None:

@@ -438,7 +438,9 @@ hjlo_status hjlo_plan_set_tolerance(hjlo_plan *p, double eta)
     // cached graph holds the old value and is rebuilt on next use
     cudaError_t e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
-    for (int a = 0; a < p->ndim; ++a) p->ax[a].eta = eta;
+    // slopes per unit length (Sec. 4.1): the second differences along axis a
+    // are compared with -eta * dx_a
+    for (int a = 0; a < p->ndim; ++a) p->ax[a].eta = eta * p->desc.dx[a];
     destroy_graph(p);
     return HJLO_OK;
 }
