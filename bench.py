@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the cost model's launch shapes")
     ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512", "adjoint512", "paper1d",
                                            "decomp"],
                     default="grid1024")
@@ -242,6 +243,8 @@ def run_sweep(args):
     Vs = [V_all[offs[i]:offs[i + 1]] for i in range(len(probs))]
     algo = {"monge": hjlo.ALGO_MONGE, "brute": hjlo.ALGO_BRUTE, "auto": hjlo.ALGO_AUTO}[args.algo]
     batch = hjlo.Batch([(p.shape, p.dx, p.h, p.P, p.W) for p in probs], algo=algo)
+    # every group's launch shapes from the library's autotuner (untimed)
+    tune = None if args.no_autotune else batch.autotune(u0s, Vs, 8)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
@@ -333,7 +336,7 @@ def run_sweep(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "sweep512", "instances": len(allp), "nsteps": nsteps,
                            "sizes": sorted(set(p.shape[0] for p in allp)), "h": 0.02, "W": "N/16",
-                           "launch_groups": groups, "updates_per_step": updates,
+                           "launch_groups": groups, "updates_per_step": updates, "autotune": tune,
                            "l2": "256 MiB buffer written between timed steps",
                            "parallelism": "instances sharded over ranks" if world > 1 else "single GPU"},
                 "per_instance_loop": loop,
@@ -607,6 +610,9 @@ def run_ours(args):
     u0 = torch.tensor(p.u0, dtype=tdt, device=dev)
     Vt = torch.tensor(p.V, dtype=torch.float64, device=dev)
     u = torch.empty_like(u0)
+    # launch shapes chosen by the library's autotuner on the first time steps
+    # (outside the timed region; results do not depend on the shape)
+    tune = plan.autotune(u0, Vt, 16) if (info["algo"] == "monge" and not args.no_autotune) else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
@@ -696,7 +702,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": {"workload": p.name, "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
                            "h": p.h, "P": list(p.P), "algo": info["algo"],
-                           "updates_per_step": updates,
+                           "updates_per_step": updates, "autotune": tune,
                            "l2": "256 MiB buffer written between timed steps; the grid is L2-resident "
                                  "within a step when it fits",
                            "parallelism": "replicas" if world > 1 else "single GPU"},

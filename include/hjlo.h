@@ -136,6 +136,16 @@ typedef struct {
  */
 hjlo_status hjlo_plan_create(const hjlo_desc *desc, void *cuda_stream, hjlo_plan **out);
 
+/* What an autotuning call chose (host struct; see hjlo_plan_autotune). */
+typedef struct {
+    int32_t lanes_per_line[HJLO_MAX_DIM]; /* monotone search: lanes per line (0: axis not tuned) */
+    int32_t lines_per_tile[HJLO_MAX_DIM]; /* lines per CTA */
+    int32_t offload[HJLO_MAX_DIM];        /* 1: wide brackets searched by warp groups */
+    int32_t trials;                       /* launch shapes timed */
+    double ms_initial;                    /* trial run with the starting shapes (ms) */
+    double ms_tuned;                      /* trial run with the chosen shapes (ms) */
+} hjlo_tune_report;
+
 /* Release a plan and everything it owns.  NULL is accepted.  Synchronises
  * the plan's stream first. */
 hjlo_status hjlo_plan_destroy(hjlo_plan *plan);
@@ -153,6 +163,22 @@ hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
  * eta negative or not finite).
  */
 hjlo_status hjlo_plan_set_tolerance(hjlo_plan *plan, double eta);
+
+/*
+ * Autotune the launch shapes of a plan's monotone passes (no counterpart in
+ * the paper: results never depend on the launch shape, only the time does).
+ * Axis by axis, shapes around the current one -- lanes per line and lines
+ * per tile halved / kept / doubled, wide-bracket offload on / off -- are
+ * timed with CUDA events on nsteps steps from a device copy of u (u itself
+ * is not modified; V: npts binary64 or NULL), and each axis keeps the
+ * fastest (a candidate must beat the incumbent by 2 %).  Synchronous; the
+ * plan's cached graph is rebuilt on next use.  report (host, may be NULL)
+ * receives the choice.  Brute-force and decomposition axes are left as they
+ * are.  Errors: HJLO_EINVAL (NULL plan/u, nsteps < 1), HJLO_ENOMEM,
+ * HJLO_ECUDA.
+ */
+hjlo_status hjlo_plan_autotune(hjlo_plan *plan, const void *u, const double *V, int64_t nsteps,
+                               hjlo_tune_report *report);
 
 /*
  * One time step (eq. eqconvol): u_out = T(u_in).  u_in and u_out hold npts
@@ -257,6 +283,15 @@ hjlo_status hjlo_batch_hbar(hjlo_batch *batch, const void *const *u0, const void
 
 /* hjlo_sync for a batch. */
 hjlo_status hjlo_batch_sync(hjlo_batch *batch, hjlo_counters *out);
+
+/*
+ * hjlo_plan_autotune for a batch: the shape of every launch group's monotone
+ * passes is tuned by timing nsteps steps of the whole batch (all groups
+ * together, as they run) from device copies of u[i].  report's per-axis
+ * fields describe the group with the most points.
+ */
+hjlo_status hjlo_batch_autotune(hjlo_batch *batch, const void *const *u, const double *const *V, int64_t nsteps,
+                                hjlo_tune_report *report);
 
 /* Number of launch groups the batch formed (0 for NULL). */
 int32_t hjlo_batch_groups(const hjlo_batch *batch);

@@ -427,6 +427,94 @@ hjlo_status hjlo_hbar(hjlo_plan *p, const void *u0, const void *un, int64_t nste
     return HJLO_OK;
 }
 
+hjlo_status hjlo_plan_autotune(hjlo_plan *p, const void *u, const double *V, int64_t nsteps, hjlo_tune_report *report)
+{
+    hjlo_status s = check_plan(p);
+    if (s != HJLO_OK) return s;
+    if (!u) return set_error(HJLO_EINVAL, "u is NULL");
+    if (nsteps < 1) return set_error(HJLO_EINVAL, "nsteps must be >= 1");
+    if ((s = set_device(p)) != HJLO_OK) return s;
+    DeviceFacts df;
+    if ((s = device_facts(df)) != HJLO_OK) return s;
+    const size_t bytes = (size_t)p->npts * p->esize;
+    void *scratch = nullptr;
+    if ((s = dmalloc(&scratch, bytes, "cudaMalloc(autotune scratch)")) != HJLO_OK) return s;
+    const double *hv = nullptr;
+    if (V) {
+        if ((s = form_hv(p, V)) != HJLO_OK) { cudaFree(scratch); return s; }
+        hv = p->d_hv;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // best of two timed runs of nsteps from a fresh copy of u
+    auto trial = [&](float *ms) -> hjlo_status {
+        float best = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            cudaError_t ce = cudaMemcpyAsync(scratch, u, bytes, cudaMemcpyDeviceToDevice, p->stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, p->stream);
+            if (ce != cudaSuccess) return cuda_error(ce, "autotune trial");
+            for (long long n = 0; n < nsteps; ++n) {
+                hjlo_status ts = enqueue_step(p, scratch, scratch, hv, 0.0, nullptr, p->stream);
+                if (ts != HJLO_OK) return ts;
+            }
+            ce = cudaEventRecord(e1, p->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            if (ce != cudaSuccess) return cuda_error(ce, "autotune timing");
+            best = std::min(best, t);
+        }
+        *ms = best;
+        return HJLO_OK;
+    };
+    hjlo_tune_report rep;
+    memset(&rep, 0, sizeof(rep));
+    float ms0 = 0.0f;
+    if (e != cudaSuccess) s = cuda_error(e, "cudaEventCreate");
+    if (s == HJLO_OK) s = trial(&ms0);
+    float cur = ms0;
+    for (int a = 0; a < p->ndim && s == HJLO_OK; ++a) {
+        if (p->ax[a].algo != KALGO_MONGE) continue;
+        AxisPlan best = p->ax[a];
+        for (const ShapeHints &h : tune_candidates(p->ax[a])) {
+            AxisPlan t = p->ax[a];
+            if (shape_launch(t, p->esize, KALGO_MONGE, df.num_sms, df.smem_optin, 1, &h) != HJLO_OK) continue;
+            if (t.lpl == best.lpl && t.C == best.C && t.wide_mul == best.wide_mul && t.wide_add == best.wide_add)
+                continue;
+            AxisPlan keep = p->ax[a];
+            p->ax[a] = t;
+            float ms = 0.0f;
+            s = trial(&ms);
+            p->ax[a] = keep;
+            if (s != HJLO_OK) break;
+            ++rep.trials;
+            if (ms < 0.98f * cur) {
+                cur = ms;
+                best = t;
+            }
+        }
+        p->ax[a] = best;
+    }
+    float ms1 = cur;
+    if (s == HJLO_OK) s = trial(&ms1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(scratch);
+    destroy_graph(p);
+    if (s != HJLO_OK) return s;
+    for (int a = 0; a < p->ndim; ++a) {
+        if (p->ax[a].algo != KALGO_MONGE) continue;
+        rep.lanes_per_line[a] = p->ax[a].lpl;
+        rep.lines_per_tile[a] = p->ax[a].C;
+        rep.offload[a] = (p->ax[a].wide_add < (1 << 20)) ? 1 : 0;
+    }
+    rep.ms_initial = ms0;
+    rep.ms_tuned = ms1;
+    if (report) *report = rep;
+    return HJLO_OK;
+}
+
 hjlo_status hjlo_plan_set_tolerance(hjlo_plan *p, double eta)
 {
     hjlo_status s = check_plan(p);

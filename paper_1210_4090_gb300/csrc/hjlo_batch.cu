@@ -164,6 +164,35 @@ void release(hjlo_batch *b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
 }
 
+// Copy a launch shape onto a group and every member of it (their tables and
+// window offsets stay their own).
+void apply_group_shape(hjlo_batch *b, Group &g, int a, const AxisPlan &ax)
+{
+    for (int i : g.members) {
+        AxisPlan &m = b->inst[(size_t)i * b->ndim + a];
+        AxisPlan keep = m;
+        m = ax;
+        m.d_kr64 = keep.d_kr64;
+        m.dlo = keep.dlo;
+        m.dhi = keep.dhi;
+        m.centre = keep.centre;
+        m.hoff = keep.hoff;
+        m.kmin = keep.kmin;
+        m.kmax = keep.kmax;
+        m.curv = keep.curv;
+    }
+    g.ax[a] = ax;
+    g.ax[a].d_kr64 = nullptr;
+}
+
+void drop_graphs(hjlo_batch *b)
+{
+    if (b->graph_many) cudaGraphExecDestroy(b->graph_many);
+    if (b->graph_one) cudaGraphExecDestroy(b->graph_one);
+    b->graph_many = nullptr;
+    b->graph_one = nullptr;
+}
+
 // One step of every instance: each group on its own stream, forked from and
 // joined back into `st`.
 hjlo_status enqueue_batch_step(hjlo_batch *b, cudaStream_t st, int nsteps_inner)
@@ -282,29 +311,14 @@ hjlo_status hjlo_batch_create(const hjlo_desc *descs, int32_t count, void *cuda_
         const int rep = g.members[0];
         for (int a = 0; a < b->ndim && s == HJLO_OK; ++a) {
             AxisPlan ax = b->inst[(size_t)rep * b->ndim + a];
-            s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size());
+            s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size(), nullptr);
             if (s == HJLO_EUNSUPPORTED && ax.algo == KALGO_MONGE && b->descs[rep].algo == HJLO_ALGO_AUTO) {
                 // lines too long for the monotone search's shared memory
                 ax.algo = KALGO_BRUTE;
                 s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size());
             }
             if (s != HJLO_OK) break;
-            // copy the shape onto every member (their tables/offsets stay their own)
-            for (int i : g.members) {
-                AxisPlan &m = b->inst[(size_t)i * b->ndim + a];
-                AxisPlan keep = m;
-                m = ax;
-                m.d_kr64 = keep.d_kr64;
-                m.dlo = keep.dlo;
-                m.dhi = keep.dhi;
-                m.centre = keep.centre;
-                m.hoff = keep.hoff;
-                m.kmin = keep.kmin;
-                m.kmax = keep.kmax;
-                m.curv = keep.curv;
-            }
-            g.ax[a] = ax;
-            g.ax[a].d_kr64 = nullptr;
+            apply_group_shape(b, g, a, ax);
             cudaError_t e = cudaMalloc(&g.d_items[a], sizeof(BatchItem) * g.members.size());
             if (e != cudaSuccess) { s = cuda_error(e, "cudaMalloc(batch items)"); break; }
             g.h_items[a].resize(g.members.size());
@@ -403,6 +417,130 @@ hjlo_status hjlo_batch_run(hjlo_batch *b, void *const *u, const double *const *V
         if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
     }
     b->steps += nsteps;
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_batch_autotune(hjlo_batch *b, const void *const *u, const double *const *V, int64_t nsteps,
+                                hjlo_tune_report *report)
+{
+    if (!b) return set_error(HJLO_EINVAL, "batch is NULL");
+    if (!u) return set_error(HJLO_EINVAL, "u is NULL");
+    if (nsteps < 1) return set_error(HJLO_EINVAL, "nsteps must be >= 1");
+    for (int i = 0; i < b->count; ++i)
+        if (!u[i]) return set_error(HJLO_EINVAL, "u[%d] is NULL", i);
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+    DeviceFacts df;
+    hjlo_status s = device_facts(df);
+    if (s != HJLO_OK) return s;
+    // device copies of every instance, refreshed before each trial
+    long long tot = 0;
+    std::vector<long long> off(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        off[i] = tot;
+        tot += (b->npts[i] * b->esize + 255) & ~255LL;
+    }
+    char *scratch = nullptr;
+    e = cudaMalloc(&scratch, (size_t)std::max(1LL, tot));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(autotune scratch)");
+    std::vector<void *> su(b->count);
+    for (int i = 0; i < b->count; ++i) su[i] = scratch + off[i];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) s = cuda_error(e, "cudaEventCreate");
+    auto refresh = [&]() -> hjlo_status {
+        for (int i = 0; i < b->count; ++i) {
+            cudaError_t ce = cudaMemcpyAsync(su[i], u[i], (size_t)(b->npts[i] * b->esize), cudaMemcpyDeviceToDevice,
+                                             b->stream);
+            if (ce != cudaSuccess) return cuda_error(ce, "autotune copy");
+        }
+        return HJLO_OK;
+    };
+    // one untimed step (rebuilds the graphs of a new shape), then the best of
+    // two timed runs of nsteps
+    auto trial = [&](float *ms) -> hjlo_status {
+        hjlo_status ts = refresh();
+        if (ts == HJLO_OK) ts = hjlo_batch_run(b, su.data(), V, 1);
+        float best = 1e30f;
+        for (int r = 0; r < 2 && ts == HJLO_OK; ++r) {
+            if ((ts = refresh()) != HJLO_OK) break;
+            cudaError_t ce = cudaEventRecord(e0, b->stream);
+            if (ce != cudaSuccess) return cuda_error(ce, "autotune timing");
+            if ((ts = hjlo_batch_run(b, su.data(), V, nsteps)) != HJLO_OK) break;
+            ce = cudaEventRecord(e1, b->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            if (ce != cudaSuccess) return cuda_error(ce, "autotune timing");
+            best = std::min(best, t);
+        }
+        *ms = best;
+        return ts;
+    };
+    hjlo_tune_report rep;
+    memset(&rep, 0, sizeof(rep));
+    const long long steps0 = b->steps;      // trials do not count as steps of the batch
+    float ms0 = 0.0f;
+    if (s == HJLO_OK) s = trial(&ms0);
+    float cur = ms0;
+    // groups by decreasing work, axis by axis
+    std::vector<size_t> order(b->groups.size());
+    std::vector<long long> work(b->groups.size(), 0);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        order[gi] = gi;
+        for (int i : b->groups[gi].members) work[gi] += b->npts[i];
+    }
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work[x] > work[y]; });
+    for (size_t gi : order) {
+        Group &g = b->groups[gi];
+        for (int a = 0; a < b->ndim && s == HJLO_OK; ++a) {
+            if (g.ax[a].algo != KALGO_MONGE) continue;
+            AxisPlan best = g.ax[a];
+            const AxisPlan start = g.ax[a];
+            for (const ShapeHints &h : tune_candidates(start)) {
+                AxisPlan t = start;
+                if (shape_launch(t, b->esize, KALGO_MONGE, df.num_sms, df.smem_optin, (long long)g.members.size(),
+                                 &h) != HJLO_OK)
+                    continue;
+                if (t.lpl == best.lpl && t.C == best.C && t.wide_mul == best.wide_mul && t.wide_add == best.wide_add)
+                    continue;
+                apply_group_shape(b, g, a, t);
+                drop_graphs(b);
+                float ms = 0.0f;
+                s = trial(&ms);
+                if (s != HJLO_OK) break;
+                ++rep.trials;
+                if (ms < 0.98f * cur) {
+                    cur = ms;
+                    best = t;
+                }
+            }
+            apply_group_shape(b, g, a, best);
+            drop_graphs(b);
+        }
+        if (s != HJLO_OK) break;
+    }
+    float ms1 = cur;
+    if (s == HJLO_OK) s = trial(&ms1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(scratch);
+    b->steps = steps0;
+    if (s != HJLO_OK) return s;
+    if (!order.empty()) {
+        const Group &g = b->groups[order[0]];
+        for (int a = 0; a < b->ndim; ++a) {
+            if (g.ax[a].algo != KALGO_MONGE) continue;
+            rep.lanes_per_line[a] = g.ax[a].lpl;
+            rep.lines_per_tile[a] = g.ax[a].C;
+            rep.offload[a] = (g.ax[a].wide_add < (1 << 20)) ? 1 : 0;
+        }
+    }
+    rep.ms_initial = ms0;
+    rep.ms_tuned = ms1;
+    if (report) *report = rep;
     return HJLO_OK;
 }
 

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "hjlo.h"
 #include "hjlo_device.cuh"
@@ -44,10 +45,27 @@ double kernel_entry(long long d, double dx, double h, double P);
 hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W, AxisPlan &ax,
                          double **kr64_host);
 
+// Explicit launch-shape choices (0 / negative: the cost model decides).
+struct ShapeHints {
+    int lpl = 0;                 // MONGE lanes per line (power of two <= N)
+    int C = 0;                   // lines per tile (power of two)
+    int wide_mul = -1;           // offload rule of wide brackets (wide_mul, wide_add);
+    int wide_add = -1;           // wide_mul = 0 with a huge wide_add turns it off
+};
+
+// The tuning overrides of the environment (HJLO_LANES_PER_LINE,
+// HJLO_LINES_PER_TILE, HJLO_OFFLOAD) as hints.
+ShapeHints env_hints();
+
 // Chooses lines per tile, lanes per line and shared-memory layout; `replicas`
-// grids of this shape run in the same launch (batched passes).
+// grids of this shape run in the same launch (batched passes).  `hints`
+// (null: the environment's) override the cost model where they are valid.
 hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
-                         long long replicas = 1);
+                         long long replicas = 1, const ShapeHints *hints = nullptr);
+
+// Candidate shapes around ax's current one for the autotuner: lanes per line
+// and lines per tile halved / kept / doubled, offload on / off.
+std::vector<ShapeHints> tune_candidates(const AxisPlan &ax);
 
 // 3D TMA descriptor {inner, N, outer} of `ptr` for lines along a strided
 // axis; false if TMA cannot serve this pointer/shape.

@@ -186,8 +186,50 @@ static int pivot_group(int weff, int S, int lpl, double *cost)
     return best;
 }
 
-hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin, long long replicas)
+ShapeHints env_hints()
 {
+    ShapeHints h;
+    if (const char *e = getenv("HJLO_LANES_PER_LINE")) h.lpl = atoi(e);
+    if (const char *e = getenv("HJLO_LINES_PER_TILE")) h.C = atoi(e);
+    if (const char *e = getenv("HJLO_OFFLOAD")) {
+        int m = 0, a = 0;
+        if (sscanf(e, "%d,%d", &m, &a) == 2 && m >= 0 && a >= 0) {
+            h.wide_mul = m;
+            h.wide_add = a;
+        } else {
+            h.wide_mul = 0;
+            h.wide_add = 1 << 24;
+        }
+    }
+    return h;
+}
+
+std::vector<ShapeHints> tune_candidates(const AxisPlan &ax)
+{
+    std::vector<ShapeHints> out;
+    const int lpls[3] = {ax.lpl / 2, ax.lpl, ax.lpl * 2};
+    const int Cs[3] = {ax.C / 2, ax.C, ax.C * 2};
+    for (int li = 0; li < 3; ++li) {
+        if (lpls[li] < 1 || lpls[li] > 1024 || lpls[li] > ax.N) continue;
+        for (int ci = 0; ci < 3; ++ci) {
+            if (Cs[ci] < 1) continue;
+            for (int off = 0; off < 2; ++off) {
+                ShapeHints h;
+                h.lpl = lpls[li];
+                h.C = Cs[ci];
+                h.wide_mul = off ? 0 : 2;
+                h.wide_add = off ? (1 << 24) : 8;
+                out.push_back(h);
+            }
+        }
+    }
+    return out;
+}
+
+hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin, long long replicas,
+                         const ShapeHints *hints)
+{
+    const ShapeHints hint = hints ? *hints : env_hints();
     ax.algo = algo;
     ax.layout = (ax.inner == 1) ? LAYOUT_CONTIG : LAYOUT_STRIDED;
     const long long N = ax.N;
@@ -215,10 +257,9 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
         // lanes per line: maximise (occupancy efficiency) / (work per row), with
         // work per row ~ weff/S + log2(S) + 3 (pivot share, divide and conquer,
         // staging and write-back) and occupancy bounded by shared memory per
-        // line; an environment override serves tuning experiments.
+        // line; a hint (the autotuner, or the environment) overrides it.
         int best_lpl = 1;
         double best_score = -1.0;
-        const char *env = getenv("HJLO_LANES_PER_LINE");
         for (int lpl = 1; lpl <= 1024; lpl *= 2) {
             int S = odd_at_least((N + lpl - 1) / lpl);
             AxisPlan t = ax;
@@ -234,7 +275,7 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
             pivot_group(ax.weff, S, lpl, &pcost);
             double work = pcost / S + std::log2((double)S) + 3.0;
             double score = eff / work;
-            if (env && atoi(env) == lpl && lpl <= N) { best_lpl = lpl; break; }
+            if (hint.lpl == lpl && lpl <= N) { best_lpl = lpl; break; }
             if (S >= 3 && score > best_score * 1.0001) { best_score = score; best_lpl = lpl; }
         }
         // staging and write-back assume every lane of a line owns at most one
@@ -244,18 +285,12 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
         ax.log2lpl = ilog2(best_lpl);
         ax.seg = odd_at_least((N + best_lpl - 1) / best_lpl);
         ax.gs = pivot_group(ax.weff, ax.seg, ax.lpl, nullptr);
-        // tuning override "mul,add" of the offload rule; "0" turns it off
+        // offload rule of wide brackets: 2 x expected span + 8 unless hinted
         ax.wide_mul = 2;
         ax.wide_add = 8;
-        if (const char *e = getenv("HJLO_OFFLOAD")) {
-            int m = 0, a = 0;
-            if (sscanf(e, "%d,%d", &m, &a) == 2 && m >= 0 && a >= 0) {
-                ax.wide_mul = m;
-                ax.wide_add = a;
-            } else {
-                ax.wide_mul = 0;
-                ax.wide_add = 1 << 24;
-            }
+        if (hint.wide_mul >= 0 && hint.wide_add >= 0) {
+            ax.wide_mul = hint.wide_mul;
+            ax.wide_add = hint.wide_add;
         }
         ax.lp = halo_pitch(ax);
         ax.wpl = 1;
@@ -293,9 +328,9 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
         if (t.smem > budget) break;
         C *= 2;
     }
-    // tuning override of the lines per tile (a power of two that fits)
-    if (const char *e = getenv("HJLO_LINES_PER_TILE")) {
-        const int want = atoi(e);
+    // hinted lines per tile (a power of two that fits)
+    if (hint.C > 0) {
+        const int want = hint.C;
         if (want >= cmin && (want & (want - 1)) == 0 && (long long)want * lanes <= 1024) {
             AxisPlan t = ax;
             t.C = want;

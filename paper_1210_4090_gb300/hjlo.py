@@ -45,6 +45,16 @@ class Counters(ctypes.Structure):
                 ("error_flags", _i32), ("reserved", _i32), ("components", _i64)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("lanes_per_line", _i32 * 3), ("lines_per_tile", _i32 * 3), ("offload", _i32 * 3),
+                ("trials", _i32), ("ms_initial", _f64), ("ms_tuned", _f64)]
+
+    def as_dict(self) -> dict:
+        return {"lanes_per_line": list(self.lanes_per_line), "lines_per_tile": list(self.lines_per_tile),
+                "offload": list(self.offload), "trials": self.trials, "ms_initial": self.ms_initial,
+                "ms_tuned": self.ms_tuned}
+
+
 class HjloError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         self.status = status
@@ -63,6 +73,9 @@ _SIGS = [
     ("hjlo_plan_destroy", _i32, [_vp]),
     ("hjlo_plan_info", _i32, [_vp, ctypes.POINTER(Facts)]),
     ("hjlo_plan_set_tolerance", _i32, [_vp, _f64]),
+    ("hjlo_plan_autotune", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(TuneReport)]),
+    ("hjlo_batch_autotune", _i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64,
+                                   ctypes.POINTER(TuneReport)]),
     ("hjlo_step", _i32, [_vp, _vp, _vp, _vp, _vp]),
     ("hjlo_run", _i32, [_vp, _vp, _vp, _i64]),
     ("hjlo_run_tv", _i32, [_vp, _vp, _vp, _i64]),
@@ -211,6 +224,14 @@ class Plan:
         except Exception:
             pass
 
+    def autotune(self, u, V=None, nsteps: int = 8) -> dict:
+        """Time launch shapes of the monotone passes on nsteps steps from a copy
+        of u and keep the fastest per axis (hjlo_plan_autotune); u is unchanged."""
+        r = TuneReport()
+        _check(lib().hjlo_plan_autotune(self._h, self._u(u, "u"), self._v(V), int(nsteps), ctypes.byref(r)),
+               "hjlo_plan_autotune")
+        return r.as_dict()
+
     def set_tolerance(self, eta: float):
         """Convexity tolerance of an ALGO_DECOMP plan (Sec. 4.4)."""
         _check(lib().hjlo_plan_set_tolerance(self._h, float(eta)), "hjlo_plan_set_tolerance")
@@ -352,6 +373,16 @@ class Batch:
         vp = None if Vs is None else self._ptrs(Vs, torch.float64, "V", allow_none=True)
         _check(lib().hjlo_batch_run(self._h, up, vp, int(nsteps)), "hjlo_batch_run")
         return us
+
+    def autotune(self, us, Vs=None, nsteps: int = 8) -> dict:
+        """hjlo_batch_autotune: tune every group's launch shapes on nsteps steps of
+        the whole batch from copies of us (unchanged)."""
+        import torch
+        up = self._ptrs(us, self.torch_dtype, "u")
+        vp = None if Vs is None else self._ptrs(Vs, torch.float64, "V", allow_none=True)
+        r = TuneReport()
+        _check(lib().hjlo_batch_autotune(self._h, up, vp, int(nsteps), ctypes.byref(r)), "hjlo_batch_autotune")
+        return r.as_dict()
 
     def hbar(self, u0s, uns, nsteps):
         out = (_f64 * (3 * self.count))()
