@@ -668,11 +668,28 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     achieved = alg_bytes_launch / avg_launch_s / 1e9
     traffic = profile_traffic(args.workload, info["algo"], args.dtype)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": "hjlo::pass_kernel (%s)" % info["algo"],
-            "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes_launch,
-            "avg_launch_us": avg_launch_s * 1e6,
-            "fp64_ops_per_launch": p.npts * 1.0 + (p.npts / p.ndim)}
+    if info["algo"] == "brute":
+        # brute force is bound by binary64 adds: one per window candidate per
+        # output and pass (+ the potential term); peak from the unit count:
+        # 2 binary64 adds per clock per SM (the nominal 1.25 TFLOP/s counts an
+        # FMA as two) x SMs x max SM clock
+        import torch
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        clk_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        peak_gops = 2.0 * sms * clk_mhz * 1e6 / 1e9
+        weffs = [info["dhi"][a] - info["dlo"][a] + 1 for a in range(p.ndim)]
+        adds_launch = p.npts * (sum(weffs) + 1) / p.ndim
+        ach = adds_launch / avg_launch_s / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_gops, "unit": "G fp64 add/s",
+                "frac": ach / peak_gops, "traffic": None, "kernel": "hjlo::pass_kernel (brute)",
+                "peak_kind": "derived (2 adds/clk/SM x %d SMs x %.0f MHz)" % (sms, clk_mhz),
+                "fp64_adds_per_launch": adds_launch, "avg_launch_us": avg_launch_s * 1e6}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": "hjlo::pass_kernel (%s)" % info["algo"],
+                "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes_launch,
+                "avg_launch_us": avg_launch_s * 1e6,
+                "fp64_ops_per_launch": p.npts * 1.0 + (p.npts / p.ndim)}
 
     e2e = None
     if not args.no_e2e:
