@@ -82,10 +82,12 @@ def workload(name):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the axis-pass kernel's device sources (the kernel an ncu summary
+    describes): hjlo_device.cuh and the instantiation units."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1210_4090_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".inc")):
+        if f == "hjlo_device.cuh" or f.startswith("hjlo_kern"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

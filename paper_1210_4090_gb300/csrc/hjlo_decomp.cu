@@ -10,11 +10,17 @@
 // shared memory; the slope-increment kinds of all interior points are
 // classified in parallel into two bitmaps; one thread walks the bitmaps to
 // cut the components greedily (the cut is a left-to-right dependency chain,
-// a few word operations per component); then the threads take whole
-// components and merge their outputs into per-output order-preserving keys
-// with shared-memory atomicMin, so the result does not depend on the order
-// in which components finish.  Every output value is one candidate
-// fl(u(y) + k(d)) of the scheme, so the pass is never below the scheme's.
+// a few word operations per component); then each warp takes whole
+// components and convolves one with its 32 lanes: every piece of the
+// component and of the kernel finds its place in the merged order by a
+// binary search (F(j) = the number of kernel slopes below the component's
+// slope j, and for a convex piece its running maximum, which is where
+// Algorithm 1's pointer stands when it takes piece j), so the sequential
+// merge becomes independent searches.  Outputs are merged into per-output
+// order-preserving keys with shared-memory atomicMin, so the result does not
+// depend on the order in which lanes or components finish.  Every output
+// value is one candidate fl(u(y) + k(d)) of the scheme, so the pass is never
+// below the scheme's.
 #include "hjlo_internal.h"
 
 namespace hjlo {
@@ -39,13 +45,19 @@ struct DecompParams {
     int L;                       // N + n source points
     int nwords;                  // (L + 31) / 32
     double eta;
-    int off_f, off_keys, off_cv, off_cc, off_comp, off_misc;
+    int off_f, off_r, off_keys, off_cv, off_cc, off_comp, off_fm, off_misc;
 };
 
+// Candidate v for output x = z - n.  Most candidates lose: a plain read of
+// the current key skips the atomic for them (keys only decrease, so a stale
+// read can only cause an unneeded atomic, never a missed one).
 __device__ __forceinline__ void emit(unsigned long long *keys, int n, int N, int z, double v)
 {
     const int x = z - n;
-    if (x >= 0 && x < N) atomicMin(&keys[x], dkey(v));
+    if (x >= 0 && x < N) {
+        const unsigned long long k = dkey(v);
+        if (k < *reinterpret_cast<volatile unsigned long long *>(&keys[x])) atomicMin(&keys[x], k);
+    }
 }
 
 // First point q in [from, to] whose bit is clear, or `none`.
@@ -63,42 +75,75 @@ __device__ int next_clear(const unsigned *bits, int from, int to, int none)
     }
 }
 
-// Algorithm 1 on f[0..n] and g[0..m]: vertex after i pieces of f and j of g
-// is f(i) + g(j); f's piece goes first when its slope is strictly smaller.
-__device__ void conv_convex(const double *f, int n, const double *g, int m, int s, unsigned long long *keys,
-                            int N)
+// Number of kernel slopes r[0..n) strictly below rho (r increasing).
+__device__ __forceinline__ int below(const double *r, int n, double rho)
 {
-    int i = 0, j = 0;
-    emit(keys, n, N, s, __dadd_rn(f[0], g[0]));
-    while (i + j < n + m) {
-        if (i < n && (j == m || __dsub_rn(f[i + 1], f[i]) < __dsub_rn(g[j + 1], g[j])))
-            ++i;
-        else
-            ++j;
-        emit(keys, n, N, s + i + j, __dadd_rn(f[i], g[j]));
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (r[mid] < rho) lo = mid + 1; else hi = mid;
     }
+    return lo;
 }
 
-// Convex f[0..n] by concave g[0..m], m >= 1: the first convex part, the
-// segments of g translated by alpha_j (the first vertex of f whose next slope
-// is >= rho_j; it only moves down as the slopes of g decrease), the last
-// convex part.
-__device__ void conv_concave(const double *f, int n, const double *g, int m, int s, unsigned long long *keys,
-                             int N)
+// Number of entries of the non-decreasing F[0..m) that are <= i.
+__device__ __forceinline__ int upto(const int *F, int m, int i)
 {
-    double rho = __dsub_rn(g[1], g[0]);
-    int a = 0;
-    while (a < n && !(__dsub_rn(f[a + 1], f[a]) >= rho)) ++a;
-    for (int x = 0; x <= a; ++x) emit(keys, n, N, s + x, __dadd_rn(f[x], g[0]));
-    for (int j = 0; j < m; ++j) {
-        if (j > 0) {
-            rho = __dsub_rn(g[j + 1], g[j]);
-            while (a > 0 && __dsub_rn(f[a], f[a - 1]) >= rho) --a;
-        }
-        emit(keys, n, N, s + j + a, __dadd_rn(f[a], g[j]));
-        emit(keys, n, N, s + j + 1 + a, __dadd_rn(f[a], g[j + 1]));
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (F[mid] <= i) lo = mid + 1; else hi = mid;
     }
-    for (int x = m + a; x <= m + n; ++x) emit(keys, n, N, s + x, __dadd_rn(f[x - m], g[m]));
+    return lo;
+}
+
+// One component g[0..m] (source points s..s+m) convolved by a whole warp.
+// F[0..m) is scratch.  Convex kind (Algorithm 1): Algorithm 1 takes kernel
+// pieces while their slope is strictly below the component's current one,
+// so when it takes component piece j its kernel pointer is
+// Fmax(j) = max_{j' <= j} F(j') and the vertex after it is
+// (Fmax(j), j + 1); kernel piece i is taken after J(i) = #{j : Fmax(j) <= i}
+// component pieces, giving the vertex (i + 1, J(i)).  Concave kind: alpha_j =
+// F(j) and the three parts of Theorem th:ccc.
+__device__ void conv_component_warp(const double *f, const double *r, int n, const double *g, int m, int s,
+                                    bool convex, int *F, unsigned long long *keys, int N)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < m; j += 32) F[j] = below(r, n, __dsub_rn(g[j + 1], g[j]));
+    __syncwarp();
+    if (convex || m == 0) {
+        int carry = 0;
+        for (int j0 = 0; j0 < m; j0 += 32) {
+            int v = (j0 + lane < m) ? F[j0 + lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int w = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = max(v, w);
+            }
+            v = max(v, carry);
+            if (j0 + lane < m) F[j0 + lane] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+        __syncwarp();
+        if (lane == 0) emit(keys, n, N, s, __dadd_rn(f[0], g[0]));
+        for (int j = lane; j < m; j += 32) {
+            const int i = F[j];
+            emit(keys, n, N, s + i + j + 1, __dadd_rn(f[i], g[j + 1]));
+        }
+        for (int i = lane; i < n; i += 32) {
+            const int J = upto(F, m, i);
+            emit(keys, n, N, s + i + 1 + J, __dadd_rn(f[i + 1], g[J]));
+        }
+    } else {
+        const int a0 = F[0], am = F[m - 1];
+        for (int x = lane; x <= a0; x += 32) emit(keys, n, N, s + x, __dadd_rn(f[x], g[0]));
+        for (int j = lane; j < m; j += 32) {
+            const int a = F[j];
+            emit(keys, n, N, s + j + a, __dadd_rn(f[a], g[j]));
+            emit(keys, n, N, s + j + 1 + a, __dadd_rn(f[a], g[j + 1]));
+        }
+        for (int x = m + am + lane; x <= m + n; x += 32) emit(keys, n, N, s + x, __dadd_rn(f[x - m], g[m]));
+    }
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
@@ -106,6 +151,8 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     double *g = reinterpret_cast<double *>(smem);
     double *f = reinterpret_cast<double *>(smem + p.off_f);
+    double *r = reinterpret_cast<double *>(smem + p.off_r);
+    int *fm = reinterpret_cast<int *>(smem + p.off_fm);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem + p.off_keys);
     unsigned *cv = reinterpret_cast<unsigned *>(smem + p.off_cv);
     unsigned *cc = reinterpret_cast<unsigned *>(smem + p.off_cc);
@@ -123,6 +170,7 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     for (int i = tid; i <= n; i += nthr) f[i] = p.kr64[n - i];
     for (int x = tid; x < N; x += nthr) keys[x] = ~0ull;
     __syncthreads();
+    for (int i = tid; i < n; i += nthr) r[i] = __dsub_rn(f[i + 1], f[i]);      // kernel slopes
 
     // ---- kinds of the slope increment at every interior point q:
     // convex rule (increment >= -eta) and concave rule (increment <= 0)
@@ -169,17 +217,13 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     }
     __syncthreads();
 
-    // ---- convolve the components, minimum into the keys
+    // ---- convolve the components (a warp each), minimum into the keys
     const int nc = misc[0];
-    for (int c = tid; c < nc; c += nthr) {
+    for (int c = tid >> 5; c < nc; c += nthr >> 5) {
         const int s = (int)(comp[c] & ~kConvexBit);
         const bool convex = (comp[c] & kConvexBit) != 0;
         const int e = (int)(comp[c + 1] & ~kConvexBit);
-        const int m = e - s;
-        if (convex || m == 0)
-            conv_convex(f, n, g + s, m, s, keys, N);
-        else
-            conv_concave(f, n, g + s, m, s, keys, N);
+        conv_component_warp(f, r, n, g + s, e - s, s, convex, fm + s, keys, N);
     }
     __syncthreads();
 
@@ -204,6 +248,8 @@ size_t decomp_smem(const AxisPlan &ax, DecompParams *p)
     off += sizeof(double) * L;                                  // g
     const size_t off_f = off;
     off += sizeof(double) * (n + 1);
+    const size_t off_r = off;
+    off += sizeof(double) * (n + 1);
     off = (off + 15) & ~size_t(15);
     const size_t off_keys = off;
     off += sizeof(unsigned long long) * N;
@@ -213,10 +259,14 @@ size_t decomp_smem(const AxisPlan &ax, DecompParams *p)
     off += sizeof(unsigned) * nwords;
     const size_t off_comp = off;
     off += sizeof(unsigned) * (L + 1);
+    const size_t off_fm = off;
+    off += sizeof(int) * (L + 1);
     const size_t off_misc = off;
     off += 16;
     if (p) {
         p->off_f = (int)off_f;
+        p->off_r = (int)off_r;
+        p->off_fm = (int)off_fm;
         p->off_keys = (int)off_keys;
         p->off_cv = (int)off_cv;
         p->off_cc = (int)off_cc;
