@@ -55,8 +55,12 @@ __device__ __forceinline__ void emit(unsigned long long *keys, int n, int N, int
 {
     const int x = z - n;
     if (x >= 0 && x < N) {
-        const unsigned long long k = dkey(v);
-        if (k < *reinterpret_cast<volatile unsigned long long *>(&keys[x])) atomicMin(&keys[x], k);
+        unsigned khi, klo;
+        dkey32(v, khi, klo);
+        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(&keys[x]);
+        const unsigned chi = (unsigned)(cur >> 32), clo = (unsigned)cur;
+        if (khi < chi || (khi == chi && klo < clo))       // 32-bit compares (see dkey32)
+            atomicMin(&keys[x], ((unsigned long long)khi << 32) | klo);
     }
 }
 

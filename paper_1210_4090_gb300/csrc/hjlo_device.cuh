@@ -176,13 +176,45 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned long long by
 
 // ------------------------------------------------------------------ number helpers
 
-// Order-preserving integer key of a binary64 value; -0 maps to +0's key so
-// that equal values (IEEE ==) have equal keys.  Finite inputs only.
+// Order-preserving integer key of a binary64 value, as two 32-bit words
+// (high, low): negative values have every bit flipped, the others the sign
+// bit set; -0 maps to +0's key so that equal values (IEEE ==) have equal
+// keys.  Finite inputs only.  32-bit integer instructions only: on this GPU
+// 64-bit integer compares share the binary64 pipe with the candidate adds.
+__device__ __forceinline__ void dkey32(double x, unsigned &khi, unsigned &klo)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned neg = (unsigned)((int)hi >> 31);
+    const bool mzero = (hi == 0x80000000u) && (lo == 0u);
+    khi = mzero ? 0x80000000u : (hi ^ (neg | 0x80000000u));
+    klo = mzero ? 0u : (lo ^ neg);
+}
+
+// The same key as one 64-bit word (for 64-bit atomics).
 __device__ __forceinline__ unsigned long long dkey(double x)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-    return (b == 0x8000000000000000ull) ? 0x8000000000000000ull : k;
+    unsigned khi, klo;
+    dkey32(x, khi, klo);
+    return ((unsigned long long)khi << 32) | klo;
+}
+
+// dkey held as two 32-bit words, compared and shuffled with 32-bit
+// instructions.
+struct Key2 {
+    unsigned hi, lo;
+};
+__device__ __forceinline__ Key2 key2_max() { return Key2{0xffffffffu, 0xffffffffu}; }
+__device__ __forceinline__ Key2 key2(double x)
+{
+    Key2 k;
+    dkey32(x, k.hi, k.lo);
+    return k;
+}
+__device__ __forceinline__ bool key2_less(Key2 a, Key2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool key2_eq(Key2 a, Key2 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ Key2 key2_shfl_xor(Key2 a, int w)
+{
+    return Key2{__shfl_xor_sync(0xffffffffu, a.hi, w), __shfl_xor_sync(0xffffffffu, a.lo, w)};
 }
 
 // Inverse of dkey for keys of finite values.
@@ -307,14 +339,13 @@ __device__ __forceinline__ int wrapN(int x, int N)
 // Exact scan of halo indices [lo, hi] for row r: smallest key, ascending jj.
 template <typename T, int LAYOUT>
 __device__ __forceinline__ void exact_scan(const PassParams &p, const T *su, const double *kr64, int l, int r,
-                                           int lo, int hi, unsigned long long &best, int &bt)
+                                           int lo, int hi, Key2 &best, int &bt)
 {
     const int N = (int)p.N;
     int pos = wrapN(lo + p.hoff, N);
     for (int jj = lo; jj <= hi; ++jj) {
-        double c = __dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[jj - r]);
-        unsigned long long key = dkey(c);
-        if (key < best) { best = key; bt = jj - r; }
+        const Key2 key = key2(__dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[jj - r]));
+        if (key2_less(key, best)) { best = key; bt = jj - r; }
         pos = (pos + 1 == N) ? 0 : pos + 1;
     }
 }
@@ -341,15 +372,14 @@ __device__ __forceinline__ int screened_row(const PassParams &p, const T *su, co
     // another candidate is within the screen's error: binary64 over the survivors
     ++rescans;
     const int N = (int)p.N;
-    unsigned long long best = ~0ull;
+    Key2 best = key2_max();
     int bt = t1;
     for (int t = tlo; t <= thi; ++t) {
         int c = f[t] + k[t];
         if (c <= thr) {
             int pos = wrapN(r + t + p.hoff, N);
-            double e = __dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[t]);
-            unsigned long long key = dkey(e);
-            if (key < best) { best = key; bt = t; }
+            const Key2 key = key2(__dadd_rn(widen(su[uidx<LAYOUT>(p, l, pos)]), kr64[t]));
+            if (key2_less(key, best)) { best = key; bt = t; }
         }
     }
     return bt;
@@ -416,22 +446,21 @@ __device__ __forceinline__ int row_or_offload(const PassParams &p, const T *su, 
     int res = t1;
     if (__any_sync(0xffffffffu, need)) {
         const int N = (int)p.N;
-        unsigned long long bk = ~0ull;
+        Key2 bk = key2_max();
         int bt = 0x7fffffff;
         if (need) {
             for (int tt = lob + sl; tt <= hib; tt += G) {
                 if (f[tt] + kk[tt] <= thr) {
                     const int pos = wrapN(rb + tt + p.hoff, N);
-                    const double e = __dadd_rn(widen(su[uidx<LAYOUT>(p, lnb, pos)]), kr64[tt]);
-                    const unsigned long long key = dkey(e);
-                    if (key < bk) { bk = key; bt = tt; }
+                    const Key2 key = key2(__dadd_rn(widen(su[uidx<LAYOUT>(p, lnb, pos)]), kr64[tt]));
+                    if (key2_less(key, bk)) { bk = key; bt = tt; }
                 }
             }
         }
         for (int w = G >> 1; w; w >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, w);
+            const Key2 ok = key2_shfl_xor(bk, w);
             const int ot = __shfl_xor_sync(0xffffffffu, bt, w);
-            if (ok < bk || (ok == bk && ot < bt)) { bk = ok; bt = ot; }
+            if (key2_less(ok, bk) || (key2_eq(ok, bk) && ot < bt)) { bk = ok; bt = ot; }
         }
         if (need) res = bt;
     }
@@ -650,7 +679,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         if (active && fallback) {
             // brute force, one row per lane of the line
             for (int r = g; r < N; r += lpl) {
-                unsigned long long best = ~0ull;
+                Key2 best = key2_max();
                 int bt = 0;
                 exact_scan<T, LAYOUT>(p, su, kr64, line, r, r, r + weff - 1, best, bt);
                 lt[r] = (unsigned short)bt;
@@ -692,23 +721,22 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             const bool need = hp && !(m2 > thr);
             int tpiv = t1;
             if (__any_sync(0xffffffffu, need)) {
-                unsigned long long bk = ~0ull;
+                Key2 bk = key2_max();
                 int bt = 0x7fffffff;
                 if (need) {
                     const int *f = lfx + rp;
                     for (int t = tlo; t <= thi; ++t) {
                         if (f[t] + lk[t] <= thr) {
                             int pos = wrapN(rp + t + p.hoff, N);
-                            double e = __dadd_rn(widen(su[uidx<LAYOUT>(p, line, pos)]), kr64[t]);
-                            unsigned long long key = dkey(e);
-                            if (key < bk) { bk = key; bt = t; }
+                            const Key2 key = key2(__dadd_rn(widen(su[uidx<LAYOUT>(p, line, pos)]), kr64[t]));
+                            if (key2_less(key, bk)) { bk = key; bt = t; }
                         }
                     }
                 }
                 for (int w = 1; w < GS; w <<= 1) {
-                    unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, w);
-                    int ot = __shfl_xor_sync(0xffffffffu, bt, w);
-                    if (ok < bk || (ok == bk && ot < bt)) { bk = ok; bt = ot; }
+                    const Key2 ok = key2_shfl_xor(bk, w);
+                    const int ot = __shfl_xor_sync(0xffffffffu, bt, w);
+                    if (key2_less(ok, bk) || (key2_eq(ok, bk) && ot < bt)) { bk = ok; bt = ot; }
                 }
                 if (need) tpiv = bt;
                 if (need && o == 0) ++rescans;
@@ -773,23 +801,25 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             unsigned short *lt = tt + line * p.tp;
             const int wl = warp - line * p.wpl;
             for (int r = wl; r < N; r += p.wpl) {
-                unsigned long long best = ~0ull;
+                // running minimum as a Key2: the binary64 pipe only does the adds
+                Key2 best = key2_max();
                 int bt = 0;
                 const int lo = r + lane, hi = r + weff - 1;
                 if (lo <= hi) {
                     int pos = wrapN(lo + p.hoff, N);
                     for (int jj = lo; jj <= hi; jj += 32) {
-                        double c = __dadd_rn(widen(su[uidx<LAYOUT>(p, line, pos)]), kr64[jj - r]);
-                        unsigned long long key = dkey(c);
-                        if (key < best) { best = key; bt = jj - r; }
+                        const Key2 key = key2(__dadd_rn(widen(su[uidx<LAYOUT>(p, line, pos)]), kr64[jj - r]));
+                        const bool less = key2_less(key, best);
+                        best = less ? key : best;
+                        bt = less ? jj - r : bt;
                         pos += 32;
                         while (pos >= N) pos -= N;
                     }
                 }
                 for (int o = 16; o; o >>= 1) {
-                    unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
-                    int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-                    if (ok < best || (ok == best && ot < bt)) { best = ok; bt = ot; }
+                    const Key2 ok = key2_shfl_xor(best, o);
+                    const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                    if (key2_less(ok, best) || (key2_eq(ok, best) && ot < bt)) { best = ok; bt = ot; }
                 }
                 if (lane == 0) lt[r] = (unsigned short)bt;
             }

@@ -295,7 +295,12 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
         ax.lp = halo_pitch(ax);
         ax.wpl = 1;
     } else {
-        ax.wpl = (N >= 64) ? 2 : 1;
+        // brute force: warps per line (rows interleaved) until the grid has
+        // about 48 warps per SM, at least 4 rows per warp
+        ax.wpl = 1;
+        while (ax.wpl < 16 && nlines * ax.wpl < 48LL * num_sms && 2LL * ax.wpl * 4 <= N &&
+               32LL * 2 * ax.wpl * cmin <= 512)
+            ax.wpl *= 2;
         ax.lpl = 32 * ax.wpl;
         ax.log2lpl = ilog2(ax.lpl);
         ax.seg = 1;
