@@ -399,3 +399,91 @@ def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_
             Vn = Vs[step] if V_per_step else Vs
             u = u - float(h) * Vn
     return u, ncomp
+
+
+# ---------------------------------------------------------------------------
+# The first discrete semigroup (Sec. 2.2, eq. cost1): the cost of a step is
+# the action of the straight path from the source y to the target x in time
+# tau, c(y, x) = tau K*(v) - int_0^tau V(y + s v) ds, v = (x - y)/tau, and
+# T u(x) = min_y u(y) + c(y, x) over the window box (the potential term no
+# longer separates, so there is no axis splitting).  V is a finite Fourier
+# series on the torus of side L_a = N_a dx_a,
+# V(x) = Re sum_m c_m exp(2 pi i sum_a k_ma x_a / L_a), for which the path
+# integral is exact:  tau Re sum_m c_m exp(i alpha_m(y)) phi(theta_m(D)),
+# alpha_m(y) = 2 pi sum_a k_ma y_a / L_a, theta_m(D) = 2 pi sum_a k_ma D_a / L_a,
+# D = x - y (lifted), phi(theta) = (exp(i theta) - 1)/(i theta), phi(0) = 1.
+
+def trig_values(shape, modes, coef):
+    """V on the grid points i_a dx_a of the torus (phases 2 pi k_a i_a / N_a)."""
+    shape = tuple(int(s) for s in shape)
+    grids = np.meshgrid(*[np.arange(n) / n for n in shape], indexing="ij")
+    V = np.zeros(shape)
+    for k, c in zip(np.asarray(modes).reshape(len(coef), -1), coef):
+        th = 2 * np.pi * sum(int(ka) * g for ka, g in zip(k, grids))
+        V = V + (np.real(c) * np.cos(th) - np.imag(c) * np.sin(th))
+    return V
+
+
+def path_integral(modes, coef, y, D, tau, L=1.0):
+    """int_0^tau V(y + s D / tau) ds in closed form (points y, lifted
+    displacements D, both (..., ndim) arrays; L: the torus sides)."""
+    y = np.asarray(y, dtype=np.float64) / np.asarray(L, dtype=np.float64)
+    D = np.asarray(D, dtype=np.float64) / np.asarray(L, dtype=np.float64)
+    out = 0.0
+    for k, c in zip(np.asarray(modes).reshape(len(coef), -1), coef):
+        k = k.astype(np.float64)
+        a = 2 * np.pi * (y @ k)
+        th = 2 * np.pi * (D @ k)
+        small = np.abs(th) < 1e-300
+        ths = np.where(small, 1.0, th)
+        pre = np.where(small, 1.0, np.sin(ths) / ths)
+        pim = np.where(small, 0.0, (1 - np.cos(ths)) / ths)
+        are = np.real(c) * np.cos(a) - np.imag(c) * np.sin(a)
+        aim = np.real(c) * np.sin(a) + np.imag(c) * np.cos(a)
+        out = out + (are * pre - aim * pim)
+    return tau * out
+
+
+def integral_run(u0, dx, h, P, W, modes, coef, nsteps: int = 1):
+    """nsteps of the first discrete semigroup (eq. cost1, time-independent V
+    as a Fourier series, exact path integral).  Per candidate, in binary64:
+    fl(fl(u(y) + K(d)) - fl(h * S)), K(d) = k_0[d_0] + k_1[d_1] + ... (eq.
+    cost2's kernel tables, left to right), S = sum over modes in order of
+    fl(fl(Are Pre) - fl(Aim Pim)) with A = c_m exp(i alpha_m(y)) and
+    (Pre, Pim) = phi(theta_m(D)) = (sin theta / theta, (1 - cos theta) / theta).
+    Windows as in the scheme, per axis; the minimum runs over the whole box
+    of displacements."""
+    u = np.array(u0, dtype=np.float64, copy=True)
+    shape = u.shape
+    ndim = u.ndim
+    dxv, Pv, Wv = _vec(dx, ndim, np.float64), _vec(P, ndim, np.float64), _vec(W, ndim, np.int64)
+    tabs = [table(shape[a], float(dxv[a]), float(h), float(Pv[a]), int(Wv[a])) for a in range(ndim)]
+    modes = np.asarray(modes, dtype=np.int64).reshape(len(coef), ndim)
+    grids = np.meshgrid(*[np.arange(n) / n for n in shape], indexing="ij")
+    A = []
+    for k, c in zip(modes, coef):
+        a = 2 * np.pi * sum(float(ka) * g for ka, g in zip(k, grids))
+        ca, sa = np.cos(a), np.sin(a)
+        A.append((np.real(c) * ca - np.imag(c) * sa, np.real(c) * sa + np.imag(c) * ca))
+    ranges = [range(t[0], t[1] + 1) for t in tabs]
+    idx = np.indices(shape)
+    for _ in range(nsteps):
+        best = np.full(shape, np.inf)
+        for d in np.ndindex(*[len(r) for r in ranges]):
+            dd = [ranges[a][d[a]] for a in range(ndim)]
+            Kd = 0.0
+            for a in range(ndim):
+                Kd = Kd + tabs[a][2][d[a]]
+            ys = tuple((idx[a] - dd[a]) % shape[a] for a in range(ndim))
+            S = np.zeros(shape)
+            for m, k in enumerate(modes):
+                th = 2 * np.pi * sum(float(k[a]) * dd[a] / shape[a] for a in range(ndim))
+                if th == 0.0:
+                    pre, pim = 1.0, 0.0
+                else:
+                    pre, pim = np.sin(th) / th, (1.0 - np.cos(th)) / th
+                S = S + (A[m][0][ys] * pre - A[m][1][ys] * pim)
+            cand = (u[ys] + Kd) - float(h) * S
+            best = np.minimum(best, cand)
+        u = best
+    return u
