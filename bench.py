@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-autotune", action="store_true", help="keep the cost model's launch shapes")
     ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512", "adjoint512", "paper1d",
-                                           "decomp"],
+                                           "decomp", "integral128"],
                     default="grid1024")
     ap.add_argument("--loop-instances", type=int, default=28,
                     help="sweep512: instances timed one plan at a time for the per-instance loop")
@@ -592,6 +592,66 @@ def run_decomp(args):
     print(json.dumps(line), flush=True)
 
 
+def run_integral(args):
+    """The first discrete semigroup (eq. cost1, hjlo_integral_*) on the 128^2
+    law: every candidate of the 9 x 9 window box with the exact path integral
+    of a 12-mode Fourier potential.  Bound by binary64 arithmetic:
+    4 operations per mode and candidate plus 3 per candidate."""
+    import torch
+    from paper_1210_4090_gb300 import hjlo
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    p = WL.integral128()
+    modes, coef = p.extra["modes"], p.extra["coef"]
+    plan = hjlo.IntegralPlan(p.shape, p.dx, p.h, p.P, p.W, modes, coef)
+    dev = torch.device("cuda", local)
+    u0 = torch.tensor(p.u0, device=dev)
+    u = torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        u.copy_(u0)
+        plan.run(u, p.nsteps)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        u.copy_(u0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(u, p.nsteps)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    plan.close()
+    updates = p.npts * p.nsteps
+    box = (2 * p.W[0] + 1) * (2 * p.W[1] + 1)
+    ops = float(updates) * box * (4 * len(coef) + 3)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = 2.0 * sms * 2070.0e6 / 1e9
+    ach = ops / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        O.integral_run(p.u0, p.dx, p.h, p.P, p.W, modes, coef, 2)
+        dt = time.perf_counter() - t0
+        cpu = {"value": p.npts * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "integral128, the first 2 time steps (numpy, %.1f s)" % dt}
+    line = {"metric": METRIC + " (first discrete semigroup, eq. cost1)", "value": updates / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "integral128", "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
+                       "modes": int(len(coef)), "box": box},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G fp64 op/s", "frac": ach / peak,
+                         "peak_kind": "derived (2 ops/clk/SM x %d SMs x 2070 MHz)" % sms,
+                         "fp64_ops_per_update": box * (4 * len(coef) + 3)},
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -746,6 +806,8 @@ def main():
         run_paper1d(args)
     elif args.workload == "decomp":
         run_decomp(args)
+    elif args.workload == "integral128":
+        run_integral(args)
     else:
         run_ours(args)
 

@@ -301,6 +301,38 @@ int32_t hjlo_batch_groups(const hjlo_batch *batch);
  * last call raised the corresponding flag (the flags are then cleared). */
 hjlo_status hjlo_sync(hjlo_plan *plan, hjlo_counters *out);
 
+/*
+ * The first discrete semigroup (Sec. 2.2, eq. cost1): the cost of a step is
+ * the action of the straight path from the source y to the target x in time
+ * h, c(y, x) = h K*(v) - int_0^h V(y + s v) ds, v = (x - y)/h, and
+ * u'(x) = min_y u(y) + c(y, x) over the box of the per-axis windows of
+ * desc (the potential term does not separate by axis: every candidate of
+ * the box is evaluated).  V is time-independent and given as a Fourier series
+ * on the torus of side L_a = shape[a] * dx[a]:
+ *   V(x) = Re sum_m c_m exp(2 pi i sum_a modes[m][a] x_a / L_a),
+ * for which the path integral is exact (no quadrature rule):
+ *   h Re sum_m c_m exp(i alpha_m(y)) phi(theta_m(x - y)),
+ *   phi(theta) = (exp(i theta) - 1)/(i theta).
+ * modes: nmodes * ndim int32, coef: nmodes * 2 binary64 (re, im), host,
+ * copied.  desc->dtype must be HJLO_F64, desc->algo AUTO or BRUTE.  Tables
+ * (per point and mode, per displacement) are formed on the host in binary64
+ * with the C library's sin and cos.  Errors: HJLO_EINVAL, HJLO_EUNSUPPORTED
+ * (grid x box x modes too large), HJLO_ENOMEM, HJLO_ECUDA.
+ */
+typedef struct hjlo_integral hjlo_integral;
+hjlo_status hjlo_integral_create(const hjlo_desc *desc, int32_t nmodes, const int32_t *modes, const double *coef,
+                                 void *cuda_stream, hjlo_integral **out);
+
+/* nsteps steps in place on u (npts binary64, device); a ping-pong buffer of
+ * the plan holds every other step. */
+hjlo_status hjlo_integral_run(hjlo_integral *plan, double *u, int64_t nsteps);
+
+/* Wait for the plan's stream. */
+hjlo_status hjlo_integral_sync(hjlo_integral *plan);
+
+/* Release the plan (NULL accepted). */
+hjlo_status hjlo_integral_destroy(hjlo_integral *plan);
+
 /* Largest window (displacements per axis, after resolving W) served by
  * hjlo_step_noalloc. */
 #define HJLO_NOALLOC_MAX_WINDOW 8192

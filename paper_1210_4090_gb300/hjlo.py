@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Plan", "Batch", "HjloError", "lib", "library_path", "exported_symbols", "step_noalloc",
+__all__ = ["Plan", "Batch", "IntegralPlan", "HjloError", "lib", "library_path", "exported_symbols", "step_noalloc",
            "F64", "F32_STORAGE", "ALGO_AUTO", "ALGO_BRUTE", "ALGO_MONGE", "ALGO_DECOMP"]
 
 F64, F32_STORAGE = 0, 1
@@ -74,6 +74,11 @@ _SIGS = [
     ("hjlo_plan_info", _i32, [_vp, ctypes.POINTER(Facts)]),
     ("hjlo_plan_set_tolerance", _i32, [_vp, _f64]),
     ("hjlo_plan_autotune", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(TuneReport)]),
+    ("hjlo_integral_create", _i32, [ctypes.POINTER(Desc), _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp,
+                                    ctypes.POINTER(_vp)]),
+    ("hjlo_integral_run", _i32, [_vp, _vp, _i64]),
+    ("hjlo_integral_sync", _i32, [_vp]),
+    ("hjlo_integral_destroy", _i32, [_vp]),
     ("hjlo_batch_autotune", _i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64,
                                    ctypes.POINTER(TuneReport)]),
     ("hjlo_step", _i32, [_vp, _vp, _vp, _vp, _vp]),
@@ -397,3 +402,49 @@ class Batch:
                "steps": c.steps, "error_flags": c.error_flags}
         _check(st, "hjlo_batch_sync")
         return res
+
+
+class IntegralPlan:
+    """The first discrete semigroup (eq. cost1) through hjlo_integral_*: the
+    path integral of V = Re sum_m coef[m] exp(2 pi i modes[m] . x / L) is
+    exact; every candidate of the window box is evaluated."""
+
+    def __init__(self, shape, dx, h, P, W, modes, coef, stream=None):
+        import torch
+        self.shape = tuple(int(s) for s in np.atleast_1d(shape))
+        nd = len(self.shape)
+        self.npts = int(np.prod(self.shape))
+        desc = make_desc(shape, dx, h, P, W, F64, ALGO_AUTO)
+        modes = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, nd))
+        coef = np.asarray(coef, dtype=np.complex128).reshape(-1)
+        if modes.shape[0] != coef.size:
+            raise ValueError("one coefficient per mode")
+        cf = np.ascontiguousarray(np.stack([coef.real, coef.imag], -1).reshape(-1))
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        h_ = _vp()
+        _check(lib().hjlo_integral_create(ctypes.byref(desc), int(coef.size),
+                                          modes.ctypes.data_as(ctypes.POINTER(_i32)),
+                                          cf.ctypes.data_as(ctypes.POINTER(_f64)), _vp(st), ctypes.byref(h_)),
+               "hjlo_integral_create")
+        self._h = h_
+
+    def run(self, u, nsteps: int):
+        import torch
+        if not u.is_cuda or u.dtype != torch.float64 or u.numel() != self.npts or not u.is_contiguous():
+            raise ValueError("u must be a contiguous float64 CUDA tensor of %d elements" % self.npts)
+        _check(lib().hjlo_integral_run(self._h, _vp(u.data_ptr()), int(nsteps)), "hjlo_integral_run")
+        return u
+
+    def sync(self):
+        _check(lib().hjlo_integral_sync(self._h), "hjlo_integral_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hjlo_integral_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

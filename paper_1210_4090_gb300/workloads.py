@@ -48,7 +48,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Problem", "line256", "grid1024", "cube256", "sweep512", "adjoint512",
-           "adjoint_basis", "trig_field", "pendulum", "tdep", "WORKLOADS"]
+           "adjoint_basis", "trig_field", "pendulum", "tdep", "integral128", "WORKLOADS"]
 
 
 @dataclass
@@ -224,6 +224,22 @@ def tdep(K: int = 4096, T: float = 8.0, speed: float = 4.0, nsteps: int | None =
     V = np.sin(t)[:, None] * np.cos(2.0 * x)[None, :]
     return Problem("tdep", (N,), (dx,), tau, (1.0,), (W,), n, np.cos(x), np.ascontiguousarray(V),
                    extra={"K": K, "T": tau * n, "x": x, "V_per_step": True})
+
+
+def integral128(N: int = 128, nsteps: int = 100, W: int = 4, K: int = 2, seed: int = 6) -> Problem:
+    """The first discrete semigroup's workload (eq. cost1): 2D N^2 torus,
+    dx = 1/N, h = 0.02, P = (0.3, 0.1), W per axis; V a Fourier series over
+    the half-plane modes 0 < |k|_inf <= K with cos and sin coefficients
+    ~ N(0, 0.25/|k|^2) (the 1024^2 law's, fewer modes), stored as complex
+    c_k = a_k - i b_k so that V = Re sum c_k exp(2 pi i k.x); u0 = 0."""
+    rng = np.random.default_rng(seed)
+    modes = _half_space_modes(2, K)
+    norm = np.sqrt((modes.astype(np.float64) ** 2).sum(axis=1))
+    a = rng.normal(0.0, 1.0, len(modes)) * np.sqrt(0.25) / norm
+    b = rng.normal(0.0, 1.0, len(modes)) * np.sqrt(0.25) / norm
+    coef = a - 1j * b
+    return Problem("integral128", (N, N), (1.0 / N,) * 2, 0.02, (0.3, 0.1), (W, W), nsteps,
+                   np.zeros((N, N)), None, extra={"modes": modes, "coef": coef})
 
 
 WORKLOADS = {"line256": line256, "grid1024": grid1024, "cube256": cube256,
