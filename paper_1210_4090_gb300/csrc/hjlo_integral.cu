@@ -36,7 +36,7 @@ struct hjlo_integral {
     double *d_A = nullptr;        // [2][nmodes][npts]: real parts, then imaginary parts
     double *d_K = nullptr;        // [ndisp]
     double *d_phi = nullptr;      // [ndisp][nmodes][2]
-    int *d_disp = nullptr;        // [ndisp][3] displacement per axis
+    int *d_disp = nullptr;        // [ndisp][3] displacement per axis, mod N
     double *d_tmp = nullptr;      // ping-pong buffer, npts
     long long steps = 0;
 };
@@ -50,17 +50,19 @@ __global__ void integral_kernel(const double *__restrict__ src, double *__restri
 {
     const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (x >= npts) return;
-    const long long i2 = x % n2, r = x / n2;
-    const long long i1 = r % n1, i0 = r / n1;
+    const int m0 = (int)n0, m1 = (int)n1, m2 = (int)n2;
+    const int i2 = (int)(x % n2);
+    const long long r = x / n2;
+    const int i1 = (int)(r % n1), i0 = (int)(r / n1);
     double best = INFINITY;
     for (long long di = 0; di < ndisp; ++di) {
-        long long y0 = (i0 - disp[3 * di]) % n0;
-        long long y1 = (i1 - disp[3 * di + 1]) % n1;
-        long long y2 = (i2 - disp[3 * di + 2]) % n2;
-        y0 += (y0 < 0) ? n0 : 0;
-        y1 += (y1 < 0) ? n1 : 0;
-        y2 += (y2 < 0) ? n2 : 0;
-        const long long y = (y0 * n1 + y1) * n2 + y2;
+        // periodic source coordinates: displacements are stored mod N, so
+        // one conditional add wraps them (32-bit arithmetic)
+        int y0 = i0 - disp[3 * di], y1 = i1 - disp[3 * di + 1], y2 = i2 - disp[3 * di + 2];
+        y0 += (y0 < 0) ? m0 : 0;
+        y1 += (y1 < 0) ? m1 : 0;
+        y2 += (y2 < 0) ? m2 : 0;
+        const long long y = ((long long)y0 * m1 + y1) * m2 + y2;
         double S = 0.0;
         const double *ph = phi + 2 * (long long)nmodes * di;
         for (int m = 0; m < nmodes; ++m) {
@@ -147,7 +149,11 @@ hjlo_status hjlo_integral_create(const hjlo_desc *d, int32_t nmodes, const int32
                     double k = 0.0;
                     for (int a = 0; a < d->ndim; ++a) k = k + ktab[a][tt[a]];
                     K[di] = k;
-                    for (int a = 0; a < 3; ++a) disp[3 * di + a] = (int)dd[a];
+                    // the source only depends on d mod N (K and phi keep the lift)
+                    for (int a = 0; a < 3; ++a) {
+                        long long dm = dd[a] % s->shape[a];
+                        disp[3 * di + a] = (int)(dm < 0 ? dm + s->shape[a] : dm);
+                    }
                     for (int m = 0; m < nmodes; ++m) {
                         double sarg = 0.0;
                         for (int a = 0; a < d->ndim; ++a)
