@@ -478,6 +478,45 @@ __device__ __forceinline__ int row_or_offload(const PassParams &p, const T *su, 
 
 // ------------------------------------------------------------------ the pass kernel
 
+// Write-back of rows i = i0, i0 + step, ... < i1 of one contiguous line: the
+// exact value fl(u[src] + k[d]) at the recorded argmin, minus fl(h V) when
+// the pass carries the potential term, stored (binary32: rounded), with the
+// optional argmin.  Four rows per thread at a time, their potential-term
+// loads issued together.
+template <typename T>
+__device__ __forceinline__ void write_rows_contig(const PassParams &p, const T *lu, const unsigned short *lt,
+                                                  const double *kr64, T *dst, long long xb, int i0, int i1, int step)
+{
+    const int N = (int)p.N;
+    T *gd = dst + xb;
+    const double *gh = p.hv ? p.hv + xb : nullptr;
+    int32_t *ga = p.amin ? p.amin + xb : nullptr;
+    int i = i0;
+    for (; i + 3 * step < i1; i += 4 * step) {
+        double hvb[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hvb[b] = gh ? __ldg(gh + i + b * step) : 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int ii = i + b * step;
+            const int t = lt[ii];
+            const int pos = wrapN(ii + t + p.hoff, N);
+            double m = __dadd_rn(widen(lu[pos]), kr64[t]);
+            if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, hvb[b]) : hvb[b]);
+            store_val(gd + ii, m);
+            if (ga) ga[ii] = p.dhi - t;
+        }
+    }
+    for (; i < i1; i += step) {
+        const int t = lt[i];
+        const int pos = wrapN(i + t + p.hoff, N);
+        double m = __dadd_rn(widen(lu[pos]), kr64[t]);
+        if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, gh[i]) : gh[i]);
+        store_val(gd + i, m);
+        if (ga) ga[i] = p.dhi - t;
+    }
+}
+
 // Per-line facts of the fixed-point screen, in shared memory.
 struct LineInfo {
     unsigned fref;                  // fixq32(lower bound of u, q)
@@ -501,7 +540,6 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     unsigned short *tt = reinterpret_cast<unsigned short *>(smem + p.off_t);
     double *kr64 = reinterpret_cast<double *>(smem + p.off_k64);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + p.off_misc);
-    int *scnt = reinterpret_cast<int *>(smem + p.off_misc + 8);                  // [2]
     LineInfo *li = reinterpret_cast<LineInfo *>(smem + p.off_misc + 16);         // [C]
 
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -513,8 +551,6 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
-        scnt[0] = 0;
-        scnt[1] = 0;
     }
     if (ALGO == KALGO_MONGE && tid < C) {
         li[tid].kmin = 0x7fffffff;
@@ -677,14 +713,14 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         const int o = g & (GS - 1);
         const int rp = min((g - o) * S, N);   // the group's pivot row
         if (active && fallback) {
-            // brute force, one row per lane of the line
-            for (int r = g; r < N; r += lpl) {
+            // brute force over each lane's own segment of rows
+            for (int r = s0; r < s1; ++r) {
                 Key2 best = key2_max();
                 int bt = 0;
                 exact_scan<T, LAYOUT>(p, su, kr64, line, r, r, r + weff - 1, best, bt);
                 lt[r] = (unsigned short)bt;
             }
-            if (g == 0) atomicAdd(&scnt[1], 1);
+            if (g == 0) atomicAdd(&p.counters[CNT_FALLBACK], 1ull);
         }
         if (GS == 1) {
             // P1: every segment's first row scans the whole window
@@ -793,7 +829,33 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 }
             }
         }
-        if (rescans) atomicAdd(&scnt[0], rescans);
+        {
+            const int wr = __reduce_add_sync(0xffffffffu, rescans);
+            if (lane == 0 && wr) atomicAdd(&p.counters[CNT_RESCAN], (unsigned long long)wr);
+        }
+        if (LAYOUT == LAYOUT_CONTIG) {
+            // Every row's argmin was found by a lane of the warp that owns the
+            // row's segment (divide and conquer, offload and fallback lines all
+            // stay inside the warp after P2), so each warp writes its own rows
+            // back as soon as it is done: no block barrier, coalesced stores.
+            __syncwarp();
+            T *dst = reinterpret_cast<T *>(p.dst);
+            const int nl = (lpl >= 32) ? 1 : (32 >> p.log2lpl);     // lines held by this warp
+            for (int k = 0; k < nl; ++k) {
+                int l = cl, r0 = 0, r1 = N;
+                if (lpl >= 32) {
+                    const int w0 = (g >> 5) << 5;                    // first lane of the warp in the line
+                    r0 = min(w0 * S, N);
+                    r1 = min((w0 + 32) * S, N);
+                } else {
+                    l = ((warp << 5) >> p.log2lpl) + k;
+                }
+                if (l >= tl.valid) continue;
+                write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride, r0 + lane, r1,
+                                     32);
+            }
+            return;
+        }
     } else {
         // ---- brute force: every row scanned by a whole warp, shuffle reduction
         const int line = warp / p.wpl;
@@ -832,40 +894,8 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     if (LAYOUT == LAYOUT_CONTIG) {
         const int lanes = nthr >> p.log2C;              // threads per line
         const int l = tid / lanes, sub = tid - l * lanes;
-        if (l < tl.valid) {
-            const unsigned short *lt = tt + l * p.tp;
-            const T *lu = su + l * N;
-            const long long xb = tl.base + l * tl.lstride;
-            T *gd = dst + xb;
-            const double *gh = p.hv ? p.hv + xb : nullptr;
-            int32_t *ga = p.amin ? p.amin + xb : nullptr;
-            // four outputs per thread at a time, their potential-term loads
-            // issued together
-            int i = sub;
-            for (; i + 3 * lanes < N; i += 4 * lanes) {
-                double hvb[4];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) hvb[b] = gh ? __ldg(gh + i + b * lanes) : 0.0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int ii = i + b * lanes;
-                    const int t = lt[ii];
-                    const int pos = wrapN(ii + t + p.hoff, N);
-                    double m = __dadd_rn(widen(lu[pos]), kr64[t]);
-                    if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, hvb[b]) : hvb[b]);
-                    store_val(gd + ii, m);
-                    if (ga) ga[ii] = p.dhi - t;
-                }
-            }
-            for (; i < N; i += lanes) {
-                const int t = lt[i];
-                const int pos = wrapN(i + t + p.hoff, N);
-                double m = __dadd_rn(widen(lu[pos]), kr64[t]);
-                if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, gh[i]) : gh[i]);
-                store_val(gd + i, m);
-                if (ga) ga[i] = p.dhi - t;
-            }
-        }
+        if (l < tl.valid)
+            write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride, sub, N, lanes);
     } else {
         const int l = tid & (C - 1);
         if (l < tl.valid) {
@@ -884,10 +914,6 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 if (p.amin) p.amin[x] = p.dhi - t;
             }
         }
-    }
-    if (ALGO == KALGO_MONGE && tid == 0) {
-        if (scnt[0]) atomicAdd(&p.counters[CNT_RESCAN], (unsigned long long)scnt[0]);
-        if (scnt[1]) atomicAdd(&p.counters[CNT_FALLBACK], (unsigned long long)scnt[1]);
     }
 }
 
