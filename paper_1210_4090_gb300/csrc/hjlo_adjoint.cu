@@ -16,9 +16,10 @@
 // as the definition's sequential scatter, so ubar_0 and Vbar are reproduced
 // bit for bit and no atomics are needed.  A line whose argmins are not
 // monotone (possible only where the Monge rounding margin failed) is done by
-// one thread scattering sequentially.  Pbar is summed per line in ascending i
-// and the lines are folded in a fixed order (deterministic; its rounding
-// order differs from a single running sum).
+// one thread scattering sequentially.  Pbar is summed per line by a warp
+// (strided partial sums, then a fixed butterfly) and the lines are folded in
+// a fixed order (deterministic; its rounding order differs from a single
+// running sum).
 //
 // Memory: forward states are checkpointed every S steps; each segment is
 // recomputed once with argmin recording (S x ndim x npts int32) and then
@@ -133,27 +134,33 @@ __global__ void __launch_bounds__(256) adjoint_pass_kernel(AdjParams p)
             for (int i = lf[N]; i < lf[N + 1]; ++i) s = __dadd_rn(s, lm[i]);
         p.ub[base + l * lstride + (long long)r * pstride] = s;
     }
-    // lines with non-monotone argmins: one thread scatters in ascending i;
-    // P partial of every line: one thread sums its terms in ascending i
-    if (tid < valid) {
+    // lines with non-monotone argmins: one thread scatters in ascending i
+    if (tid < valid && !mono[tid]) {
         const int l = tid;
         const double *lm = mb + l * N;
         const int *la = a + l * N;
-        if (!mono[l]) {
-            for (int r = 0; r < N; ++r) p.ub[base + l * lstride + (long long)r * pstride] = 0.0;
-            for (int i = 0; i < N; ++i) {
-                int r = la[i] % N;
-                if (r < 0) r += N;
-                double *dst = p.ub + base + l * lstride + (long long)r * pstride;
-                *dst = __dadd_rn(*dst, lm[i]);
-            }
-        }
-        double s = 0.0;
+        for (int r = 0; r < N; ++r) p.ub[base + l * lstride + (long long)r * pstride] = 0.0;
         for (int i = 0; i < N; ++i) {
-            double g = __dmul_rn(-(double)(i - la[i]), p.dx);
+            int r = la[i] % N;
+            if (r < 0) r += N;
+            double *dst = p.ub + base + l * lstride + (long long)r * pstride;
+            *dst = __dadd_rn(*dst, lm[i]);
+        }
+    }
+    // P partial of every line: a warp per line, each lane sums its terms in
+    // ascending i, then a fixed butterfly (the same order on every run; every
+    // lane ends with the same sum since a + b == b + a)
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    for (int l = warp; l < valid; l += nwarps) {
+        const double *lm = mb + l * N;
+        const int *la = a + l * N;
+        double s = 0.0;
+        for (int i = lane; i < N; i += 32) {
+            const double g = __dmul_rn(-(double)(i - la[i]), p.dx);
             s = __dadd_rn(s, __dmul_rn(lm[i], g));
         }
-        p.pline[line0 + l * linestep] = s;
+        for (int o = 16; o; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane == 0) p.pline[line0 + l * linestep] = s;
     }
 }
 
