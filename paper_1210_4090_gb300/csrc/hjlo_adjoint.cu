@@ -17,9 +17,11 @@
 // bit for bit and no atomics are needed.  A line whose argmins are not
 // monotone (possible only where the Monge rounding margin failed) is done by
 // one thread scattering sequentially.  Pbar is summed per line by a warp
-// (strided partial sums, then a fixed butterfly) and the lines are folded in
-// a fixed order (deterministic; its rounding order differs from a single
-// running sum).
+// (strided partial sums, then a fixed butterfly), accumulated per line over
+// the steps, and the lines are folded once in a fixed order (deterministic;
+// its rounding order differs from a single running sum).  The potential
+// term's derivative Vbar -= h * ubar^{n+1} is taken by the step's first
+// reverse pass as it loads ubar.
 //
 // Memory: forward states are checkpointed every S steps; each segment is
 // recomputed once with argmin recording (S x ndim x npts int32) and then
@@ -37,7 +39,9 @@ namespace {
 struct AdjParams {
     double *ub;               // cotangent, updated in place
     const int32_t *amin;      // argmin displacement per point of this pass
-    double *pline;            // per-line P partials (global line order)
+    double *pline;            // per-line P partials of this axis, accumulated over steps
+    double *vbar;             // Vbar -= h * ub at load (the step's first reverse pass), or null
+    double h;
     long long N, inner, outer, ntiles, tiles_per_outer;
     int C, log2C;
     double dx;
@@ -91,8 +95,10 @@ __global__ void __launch_bounds__(256) adjoint_pass_kernel(AdjParams p)
         else { i = idx >> p.log2C; l = idx & (C - 1); }
         if (l >= valid) continue;
         long long x = base + l * lstride + (long long)i * pstride;
-        mb[l * N + i] = p.ub[x];
+        const double u = p.ub[x];
+        mb[l * N + i] = u;
         a[l * N + i] = i - p.amin[x];
+        if (p.vbar) p.vbar[x] = __dsub_rn(p.vbar[x], __dmul_rn(p.h, u));
     }
     __syncthreads();
     // monotone argmins (lifted), and within one period of the first
@@ -160,20 +166,16 @@ __global__ void __launch_bounds__(256) adjoint_pass_kernel(AdjParams p)
             s = __dadd_rn(s, __dmul_rn(lm[i], g));
         }
         for (int o = 16; o; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
-        if (lane == 0) p.pline[line0 + l * linestep] = s;
+        if (lane == 0) {
+            double *acc = p.pline + line0 + l * linestep;
+            *acc = __dadd_rn(*acc, s);
+        }
     }
 }
 
-// Vbar = Vbar - h*ubar (the potential term's derivative, accumulated over steps)
-__global__ void vbar_kernel(double *__restrict__ vbar, const double *__restrict__ ub, double h, long long n)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        vbar[i] = __dsub_rn(vbar[i], __dmul_rn(h, ub[i]));
-}
-
-// Pbar[axis] += sum of the per-line partials, in a fixed order: 256 threads
-// sum contiguous chunks, then a fixed pairwise tree.
+// Pbar[axis] += sum of the per-line partials (each accumulated over all steps
+// by the adjoint passes), in a fixed order: 256 threads sum contiguous
+// chunks, then a fixed pairwise tree.
 __global__ void pbar_fold_kernel(const double *__restrict__ pline, long long nlines, double *__restrict__ pbar)
 {
     __shared__ double sh[256];
@@ -267,13 +269,15 @@ hjlo_status adjoint_prepare(const hjlo_plan *p, const DeviceFacts &df)
 }
 
 hjlo_status launch_adjoint_pass(const AxisPlan &ax, double dx, double *ub, const int32_t *amin, double *pline,
-                                double *pbar_axis, int num_sms, cudaStream_t st)
+                                double *vbar, double h, int num_sms, cudaStream_t st)
 {
     AdjShape sh = adj_shape(ax, num_sms);
     AdjParams p;
     p.ub = ub;
     p.amin = amin;
     p.pline = pline;
+    p.vbar = vbar;
+    p.h = h;
     p.N = ax.N;
     p.inner = ax.inner;
     p.outer = ax.outer;
@@ -286,7 +290,6 @@ hjlo_status launch_adjoint_pass(const AxisPlan &ax, double dx, double *ub, const
         adjoint_pass_kernel<LAYOUT_CONTIG><<<(unsigned)sh.ntiles, sh.threads, sh.smem, st>>>(p);
     else
         adjoint_pass_kernel<LAYOUT_STRIDED><<<(unsigned)sh.ntiles, sh.threads, sh.smem, st>>>(p);
-    pbar_fold_kernel<<<1, 256, 0, st>>>(pline, sh.nlines, pbar_axis);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "adjoint pass launch");
     return HJLO_OK;
@@ -336,7 +339,7 @@ hjlo_status hjlo_adjoint(hjlo_plan *p, const double *u0, const double *V, int64_
         return s;
     if ((s = ensure((void **)&p->d_work, &p->work_cap, npts, sizeof(double), "cudaMalloc(work)")) != HJLO_OK)
         return s;
-    if ((s = ensure((void **)&p->d_pbar_part, &p->pbar_cap, maxlines + 1, sizeof(double),
+    if ((s = ensure((void **)&p->d_pbar_part, &p->pbar_cap, nd * maxlines + 1, sizeof(double),
                     "cudaMalloc(P partials)")) != HJLO_OK)
         return s;
     cudaStream_t st = p->stream;
@@ -364,12 +367,14 @@ hjlo_status hjlo_adjoint(hjlo_plan *p, const double *u0, const double *V, int64_
     e = cudaMemcpyAsync(ubar_0, ubar_n, ub, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && Vbar) e = cudaMemsetAsync(Vbar, 0, ub, st);
     if (e != cudaSuccess) return cuda_error(e, "adjoint init");
+    // per-line P partials of every axis, accumulated over all steps (each
+    // line by one warp per launch, launches in order), folded once at the end
+    e = cudaMemsetAsync(p->d_pbar_part, 0, sizeof(double) * (nd * maxlines + 1), st);
+    if (e != cudaSuccess) return cuda_error(e, "P partials init");
     if (Pbar) {
         e = cudaMemsetAsync(Pbar, 0, sizeof(double) * nd, st);
         if (e != cudaSuccess) return cuda_error(e, "Pbar init");
     }
-    double *pspare = p->d_pbar_part + maxlines;   // fold target when Pbar is not wanted
-    const long long vblocks = std::min<long long>((npts + 255) / 256, 4096);
     for (long long k = nseg - 1; k >= 0; --k) {
         const long long steps = std::min(S, nsteps - k * S);
         e = cudaMemcpyAsync(p->d_work, p->d_ckpt + k * npts, ub, cudaMemcpyDeviceToDevice, st);
@@ -378,14 +383,20 @@ hjlo_status hjlo_adjoint(hjlo_plan *p, const double *u0, const double *V, int64_
             if ((s = plan_enqueue_step(p, p->d_work, p->d_work, hv, 0.0, p->d_amin + n * nd * npts, st)) != HJLO_OK)
                 return s;
         for (long long n = steps - 1; n >= 0; --n) {
-            if (Vbar) vbar_kernel<<<(unsigned)vblocks, 256, 0, st>>>(Vbar, ubar_0, p->desc.h, npts);
+            // the step's first reverse pass (last axis) also takes the
+            // potential term's derivative, Vbar -= h * ubar^{n+1}, at load
             for (int a = (int)nd - 1; a >= 0; --a) {
                 s = launch_adjoint_pass(p->ax[a], p->desc.dx[a], ubar_0, p->d_amin + (n * nd + a) * npts,
-                                        p->d_pbar_part, Pbar ? Pbar + a : pspare, df.num_sms, st);
+                                        p->d_pbar_part + a * maxlines, (a == nd - 1) ? Vbar : nullptr,
+                                        p->desc.h, df.num_sms, st);
                 if (s != HJLO_OK) return s;
             }
         }
     }
+    if (Pbar)
+        for (int a = 0; a < (int)nd; ++a)
+            pbar_fold_kernel<<<1, 256, 0, st>>>(p->d_pbar_part + a * maxlines, p->ax[a].inner * p->ax[a].outer,
+                                                Pbar + a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "adjoint");
     return HJLO_OK;
