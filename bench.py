@@ -23,7 +23,7 @@ page-locked host buffers, copies inside the timed region), roofline of the
 dominant kernel (the axis pass), the CPU oracle timed on a bounded sample of
 the same workload (cpu_baseline), SM clocks sampled during the timed region
 and the number of kernels launched.  --impl reference times the CPU oracle
-alone (the reference arm of this build).
+alone (the reference arm: the paper publishes no code).
 """
 from __future__ import annotations
 

@@ -56,7 +56,7 @@ typedef enum {
     HJLO_ECUDA = 3,         /* a CUDA runtime or driver call failed */
     HJLO_EPRECOND = 4,      /* a numerical precondition failed (see hjlo_counters) */
     HJLO_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
-    HJLO_EUNSUPPORTED = 6   /* valid request this build cannot serve (e.g. line too long) */
+    HJLO_EUNSUPPORTED = 6   /* valid request the library cannot serve (e.g. line too long) */
 } hjlo_status;
 
 typedef enum {

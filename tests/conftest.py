@@ -14,8 +14,8 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests skip cleanly where no device is visible; the full test run on the
-    # GB300 selects them with -m gpu.
+    # GPU tests skip cleanly where no device is visible; on a GB300 they are
+    # selected with -m gpu.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
