@@ -316,7 +316,8 @@ hjlo_status hjlo_sync(hjlo_plan *plan, hjlo_counters *out);
  * modes: nmodes * ndim int32, coef: nmodes * 2 binary64 (re, im), host,
  * copied.  desc->dtype must be HJLO_F64, desc->algo AUTO or BRUTE.  Tables
  * (per point and mode, per displacement) are formed on the host in binary64
- * with the C library's sin and cos.  Errors: HJLO_EINVAL, HJLO_EUNSUPPORTED
+ * with the C library's sin and cos; the sum over modes uses fused
+ * multiply-adds.  Errors: HJLO_EINVAL, HJLO_EUNSUPPORTED
  * (grid x box x modes too large), HJLO_ENOMEM, HJLO_ECUDA.
  */
 typedef struct hjlo_integral hjlo_integral;

@@ -5,17 +5,21 @@
 // where K(d) = k_0[d_0] + k_1[d_1] + ... is the kinetic action tau K*(v) of
 // eq. cost2's tables (left to right) and h * S(y, d) is the exact integral of
 // the Fourier-series potential along the straight path from y to x:
-//     S = sum_m fl(fl(Are_m(y) Pre_m(d)) - fl(Aim_m(y) Pim_m(d)))   (m in order)
+//     S = sum_m Re(A_m(y) phi_m(d)) = sum_m (Are_m Pre_m - Aim_m Pim_m)
 // with A_m(y) = c_m exp(i alpha_m(y)) and (Pre, Pim) = phi(theta_m(d)),
 // phi(theta) = (sin theta / theta, (1 - cos theta) / theta), phi(0) = (1, 0).
-// The potential term does not separate by axis, so the minimum runs over the
-// whole box; there is no monotone structure to use and every candidate is
-// evaluated (4 binary64 operations per mode, 3 more per candidate).
+// S is accumulated with fused multiply-adds in two chains (even and odd
+// modes, added at the end): two binary64 operations per mode instead of
+// four, and two independent dependency chains.  The potential term does not
+// separate by axis, so the minimum runs over the whole box; there is no
+// monotone structure to use and every candidate is evaluated.
 //
 // Tables are formed once per plan on the host (libm sin / cos): A per point
 // and mode (mode-major, so the threads of a warp read consecutive sources),
-// K and phi per displacement.  One thread per output point, ping-pong
-// buffers (a step reads its whole source before any output is final).
+// K and phi per displacement.  Four threads per output point (consecutive
+// lanes) share its displacements and merge their minima by shuffles;
+// ping-pong buffers (a step reads its whole source before any output is
+// final).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -43,36 +47,55 @@ struct hjlo_integral {
 
 namespace {
 
+constexpr int kIntegralSplit = 4;      // threads per output point
+
 __global__ void integral_kernel(const double *__restrict__ src, double *__restrict__ dst,
                                 const double *__restrict__ A, const double *__restrict__ K,
                                 const double *__restrict__ phi, const int *__restrict__ disp, long long ndisp,
                                 int nmodes, long long n0, long long n1, long long n2, long long npts, double h)
 {
-    const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (x >= npts) return;
-    const int m0 = (int)n0, m1 = (int)n1, m2 = (int)n2;
-    const int i2 = (int)(x % n2);
-    const long long r = x / n2;
-    const int i1 = (int)(r % n1), i0 = (int)(r / n1);
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long x = gt / kIntegralSplit;
+    const int part = (int)(gt % kIntegralSplit);
+    const bool live = x < npts;
     double best = INFINITY;
-    for (long long di = 0; di < ndisp; ++di) {
-        // periodic source coordinates: displacements are stored mod N, so
-        // one conditional add wraps them (32-bit arithmetic)
-        int y0 = i0 - disp[3 * di], y1 = i1 - disp[3 * di + 1], y2 = i2 - disp[3 * di + 2];
-        y0 += (y0 < 0) ? m0 : 0;
-        y1 += (y1 < 0) ? m1 : 0;
-        y2 += (y2 < 0) ? m2 : 0;
-        const long long y = ((long long)y0 * m1 + y1) * m2 + y2;
-        double S = 0.0;
-        const double *ph = phi + 2 * (long long)nmodes * di;
-        for (int m = 0; m < nmodes; ++m) {
-            const double are = A[(long long)m * npts + y], aim = A[((long long)nmodes + m) * npts + y];
-            S = __dadd_rn(S, __dsub_rn(__dmul_rn(are, ph[2 * m]), __dmul_rn(aim, ph[2 * m + 1])));
+    if (live) {
+        const int m0 = (int)n0, m1 = (int)n1, m2 = (int)n2;
+        const int i2 = (int)(x % n2);
+        const long long r = x / n2;
+        const int i1 = (int)(r % n1), i0 = (int)(r / n1);
+        for (long long di = part; di < ndisp; di += kIntegralSplit) {
+            // periodic source coordinates: displacements are stored mod N, so
+            // one conditional add wraps them (32-bit arithmetic)
+            int y0 = i0 - disp[3 * di], y1 = i1 - disp[3 * di + 1], y2 = i2 - disp[3 * di + 2];
+            y0 += (y0 < 0) ? m0 : 0;
+            y1 += (y1 < 0) ? m1 : 0;
+            y2 += (y2 < 0) ? m2 : 0;
+            const long long y = ((long long)y0 * m1 + y1) * m2 + y2;
+            const double *ph = phi + 2 * (long long)nmodes * di;
+            double se = 0.0, so = 0.0;
+            int m = 0;
+            for (; m + 1 < nmodes; m += 2) {
+                se = __fma_rn(A[(long long)m * npts + y], ph[2 * m], se);
+                se = __fma_rn(-A[((long long)nmodes + m) * npts + y], ph[2 * m + 1], se);
+                so = __fma_rn(A[(long long)(m + 1) * npts + y], ph[2 * m + 2], so);
+                so = __fma_rn(-A[((long long)nmodes + m + 1) * npts + y], ph[2 * m + 3], so);
+            }
+            if (m < nmodes) {
+                se = __fma_rn(A[(long long)m * npts + y], ph[2 * m], se);
+                se = __fma_rn(-A[((long long)nmodes + m) * npts + y], ph[2 * m + 1], se);
+            }
+            const double S = __dadd_rn(se, so);
+            const double c = __dsub_rn(__dadd_rn(src[y], K[di]), __dmul_rn(h, S));
+            best = (c < best) ? c : best;
         }
-        const double c = __dsub_rn(__dadd_rn(src[y], K[di]), __dmul_rn(h, S));
-        best = (c < best) ? c : best;
     }
-    dst[x] = best;
+    // the point's minimum over its kIntegralSplit consecutive lanes
+    for (int o = 1; o < kIntegralSplit; o <<= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        best = (ob < best) ? ob : best;
+    }
+    if (live && part == 0) dst[x] = best;
 }
 
 void release(hjlo_integral *s)
@@ -217,7 +240,7 @@ hjlo_status hjlo_integral_run(hjlo_integral *s, double *u, int64_t nsteps)
     cudaError_t e = cudaSetDevice(s->device);
     if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
     double *a = u, *b = s->d_tmp;
-    const unsigned blocks = (unsigned)((s->npts + 255) / 256);
+    const unsigned blocks = (unsigned)((s->npts * kIntegralSplit + 255) / 256);
     for (long long n = 0; n < nsteps; ++n) {
         integral_kernel<<<blocks, 256, 0, s->stream>>>(a, b, s->d_A, s->d_K, s->d_phi, s->d_disp, s->ndisp, s->nmodes,
                                                        s->shape[0], s->shape[1], s->shape[2], s->npts, s->h);

@@ -1,12 +1,15 @@
 """The first discrete semigroup (eq. cost1) on the GPU against the oracle.
 
-Every candidate is the same binary64 sequence on both sides; the per-point
-and per-displacement trigonometric tables are formed independently (the C
-library's sin / cos here, numpy's in the oracle), which may differ in the
-last bit, so values are compared to 1e-12 (1 + max|u|): a table entry off by
-one ulp moves a candidate by at most nmodes x 4 ulp x max|c| x h, far below
-it.  With V = 0 or a constant V there are no tables and the result is bit
-for bit the oracle's, and on dyadic data the fully discrete scheme's."""
+The kinetic part and the final add / multiply / subtract of a candidate are
+the same binary64 operations on both sides; the path-integral sum S differs
+in rounding (fused multiply-adds in two chains on the GPU, separate products
+and one running sum in the oracle) and the trigonometric tables are formed
+independently (the C library's sin / cos here, numpy's in the oracle), each
+of which moves a candidate by at most a few ulps of its terms:
+nmodes x 4 ulp x max|c| x h per step in all, far below the 1e-12 (1 + max|u|)
+the values are compared to.  With V = 0 or a constant V there are no tables
+and the result is bit for bit the oracle's, and on dyadic data the fully
+discrete scheme's."""
 import numpy as np
 import pytest
 
