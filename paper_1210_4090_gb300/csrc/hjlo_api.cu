@@ -261,7 +261,7 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         if (d->algo == HJLO_ALGO_BRUTE) algo = KALGO_BRUTE;
         if (d->algo == HJLO_ALGO_AUTO && (ax.weff < 8 || !(ax.curv > 0))) algo = KALGO_BRUTE;
         if (d->algo == HJLO_ALGO_DECOMP) algo = KALGO_DECOMP;
-        s = (algo == KALGO_DECOMP) ? shape_decomp(ax, df.smem_optin)
+        s = (algo == KALGO_DECOMP) ? shape_decomp(ax, df.smem_optin, df.num_sms)
                                    : shape_launch(ax, p->esize, algo, df.num_sms, df.smem_optin);
         if (s == HJLO_EUNSUPPORTED && algo == KALGO_MONGE && d->algo == HJLO_ALGO_AUTO) {
             // a line too long for the monotone search's shared-memory layout:

@@ -112,7 +112,7 @@ hjlo_status kern_batch_f32_strided(const AxisPlan &ax, const BatchItem *items, c
 
 // The paper's decomposition method as an axis pass (hjlo_decomp.cu).
 hjlo_status decomp_allow_smem();
-hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin);
+hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms);
 hjlo_status launch_decomp(const AxisPlan &ax, const void *src, void *dst, const double *hv, double hv_scale,
                           unsigned long long *counters, int *flags, cudaStream_t st);
 
