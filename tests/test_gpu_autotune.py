@@ -56,3 +56,20 @@ def test_batch_autotune_keeps_exactness():
         ref = O.run(k.cpu().numpy(), p.dx, p.h, p.P, p.W, p.V, 10)
         assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64))
     b.close()
+
+
+def test_autotune_binary32_storage():
+    """Tuning a binary32-storage plan keeps it bit-exact against the oracle's
+    binary32-storage scheme."""
+    from paper_1210_4090_gb300 import hjlo
+    p = WL.grid1024(N=160, nsteps=20, W=12)
+    u0 = p.u0.astype(np.float32)
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W, dtype=hjlo.F32_STORAGE)
+    u = torch.tensor(u0, device="cuda")
+    Vt = torch.tensor(p.V, device="cuda")
+    rep = plan.autotune(u, Vt, 4)
+    assert rep["trials"] >= 1
+    plan.run(u, Vt, 20)
+    ref = O.run(u0, p.dx, p.h, p.P, p.W, p.V, 20)
+    assert np.array_equal(u.cpu().numpy().view(np.int32), ref.view(np.int32))
+    plan.close()
