@@ -239,19 +239,19 @@ __device__ __forceinline__ int expo(double x)
 // |x| / 2^q itself is.
 __device__ __forceinline__ unsigned fixq32(double x, int q)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    int eb = (int)((hi >> 20) & 0x7ffu);
-    unsigned mh = (hi & 0xfffffu) | (eb ? 0x100000u : 0u);    // significand = mh:lo (53 bits)
-    int s = (eb ? eb : 1) - 1075 - q;                          // |x| / 2^q = significand * 2^s
-    unsigned v;
-    if (s >= 0) {
-        v = (s < 32) ? (lo << s) : 0u;
-    } else {
-        int k = -s;
-        v = (k < 32) ? __funnelshift_r(lo, mh, k) : ((k < 64) ? (mh >> (k - 32)) : 0u);
-    }
-    unsigned sg = (unsigned)((int)hi >> 31);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int eb = (int)((hi >> 20) & 0x7ffu);
+    const unsigned mh = (hi & 0xfffffu) | (eb ? 0x100000u : 0u);   // significand = mh:lo (53 bits)
+    const int k = 1075 + q - (eb ? eb : 1);                        // |x| / 2^q = significand / 2^k
+    // k > 0: the low word of significand >> k, as two clamped funnel shifts
+    // (>> min(k, 32), then >> min(k - 32, 32)), so k >= 64 gives 0;
+    // k <= 0: the low word of significand << -k (0 from 32 on).  No branches.
+    const unsigned a = __funnelshift_rc(lo, mh, (unsigned)max(k, 0));
+    const unsigned vr = __funnelshift_rc(a, 0u, (unsigned)max(k - 32, 0));
+    const unsigned vl = __funnelshift_lc(0u, lo, (unsigned)max(-k, 0));
+    const unsigned v = (k > 0) ? vr : vl;
+    const unsigned sg = (unsigned)((int)hi >> 31);
     return (v ^ sg) - sg;
 }
 
@@ -658,8 +658,9 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             L.fallback = (!finite || !(p.curv > __dmul_ru(cmax, 0x1p-49))) ? 1 : 0;
         }
         __syncthreads();
-        // ---- fixed-point halo of every line and the line's kernel table
-        const int L = N + weff - 1;
+        // ---- fixed-point halo of every line and the line's kernel table.  The
+        // halo holds N + weff - 1 entries; entry jj + N repeats entry jj (same
+        // position one period later), so each position is converted once.
         if (LAYOUT == LAYOUT_CONTIG) {
             if (cl < tl.valid) {
                 const int q = li[cl].q;
@@ -667,8 +668,10 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 int *lfx = fx + cl * p.lp;
                 const T *lu = su + cl * N;
                 int pos = (sub + p.hoff) % N;
-                for (int jj = sub; jj < L; jj += lpl) {
-                    lfx[jj] = (int)(fixq32(widen(lu[pos]), q) - fref);
+                for (int jj = sub; jj < N; jj += lpl) {
+                    const int v = (int)(fixq32(widen(lu[pos]), q) - fref);
+                    lfx[jj] = v;
+                    if (jj < weff - 1) lfx[jj + N] = v;
                     pos += lpl;                      // lpl <= N
                     pos = (pos >= N) ? pos - N : pos;
                 }
@@ -684,8 +687,10 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 int jj = tid >> p.log2C;
                 int pos = (jj + p.hoff) % N;
                 const int stepN = step % N;
-                for (; jj < L; jj += step) {
-                    lfx[jj] = (int)(fixq32(widen(su[(pos << p.log2C) + l]), q) - fref);
+                for (; jj < N; jj += step) {
+                    const int v = (int)(fixq32(widen(su[(pos << p.log2C) + l]), q) - fref);
+                    lfx[jj] = v;
+                    if (jj < weff - 1) lfx[jj + N] = v;
                     pos += stepN;
                     pos = (pos >= N) ? pos - N : pos;
                 }
