@@ -101,12 +101,18 @@ typedef struct {
 
 /* Device-side counters of a plan (host struct filled by hjlo_sync). */
 typedef struct {
-    int64_t exact_rescans;        /* outputs whose binary32 screen left >1 survivor */
+    int64_t exact_rescans;        /* outputs whose fixed-point screen left >1 survivor (binary64 re-scan) */
     int64_t brute_fallback_lines; /* lines the monotone search handed to brute force */
     int64_t steps;                /* time steps enqueued on this plan so far */
     int32_t error_flags;          /* bit 0: precondition, bit 1: wait timeout */
     int32_t reserved;
     int64_t components;           /* HJLO_ALGO_DECOMP: convex/concave components convolved */
+    int64_t window_edge_hits;     /* outputs of brute or monotone passes with a partial window
+                                     (2W+1 < N) whose argmin is its first or last displacement
+                                     (d = c - W or c + W).  Zero means no output of those passes
+                                     sat on the window's edge; a nonzero count says the window
+                                     may have cut off a smaller candidate of the full torus
+                                     window (eq. los).  Autotuner trials are not counted. */
 } hjlo_counters;
 
 /*

@@ -436,6 +436,11 @@ hjlo_status hjlo_plan_autotune(hjlo_plan *p, const void *u, const double *V, int
     if ((s = set_device(p)) != HJLO_OK) return s;
     DeviceFacts df;
     if ((s = device_facts(df)) != HJLO_OK) return s;
+    // trial launches do not count: the device counters are put back afterwards
+    unsigned long long saved[CNT_N];
+    cudaError_t se = cudaStreamSynchronize(p->stream);
+    if (se == cudaSuccess) se = cudaMemcpy(saved, p->d_counters, sizeof(saved), cudaMemcpyDeviceToHost);
+    if (se != cudaSuccess) return cuda_error(se, "autotune counter save");
     const size_t bytes = (size_t)p->npts * p->esize;
     void *scratch = nullptr;
     if ((s = dmalloc(&scratch, bytes, "cudaMalloc(autotune scratch)")) != HJLO_OK) return s;
@@ -502,6 +507,9 @@ hjlo_status hjlo_plan_autotune(hjlo_plan *p, const void *u, const double *V, int
     if (e1) cudaEventDestroy(e1);
     cudaFree(scratch);
     destroy_graph(p);
+    se = cudaStreamSynchronize(p->stream);
+    if (se == cudaSuccess) se = cudaMemcpy(p->d_counters, saved, sizeof(saved), cudaMemcpyHostToDevice);
+    if (s == HJLO_OK && se != cudaSuccess) s = cuda_error(se, "autotune counter restore");
     if (s != HJLO_OK) return s;
     for (int a = 0; a < p->ndim; ++a) {
         if (p->ax[a].algo != KALGO_MONGE) continue;
@@ -550,6 +558,7 @@ hjlo_status hjlo_sync(hjlo_plan *p, hjlo_counters *out)
         out->exact_rescans = (int64_t)c[CNT_RESCAN];
         out->brute_fallback_lines = (int64_t)c[CNT_FALLBACK];
         out->components = (int64_t)c[CNT_COMPONENTS];
+        out->window_edge_hits = (int64_t)c[CNT_EDGE];
         out->steps = p->steps;
         out->error_flags = flags;
     }

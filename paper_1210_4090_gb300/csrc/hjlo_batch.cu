@@ -433,6 +433,11 @@ hjlo_status hjlo_batch_autotune(hjlo_batch *b, const void *const *u, const doubl
     DeviceFacts df;
     hjlo_status s = device_facts(df);
     if (s != HJLO_OK) return s;
+    // trial launches do not count: the device counters are put back afterwards
+    unsigned long long saved[CNT_N];
+    e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(saved, b->d_counters, sizeof(saved), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "autotune counter save");
     // device copies of every instance, refreshed before each trial
     long long tot = 0;
     std::vector<long long> off(b->count);
@@ -525,9 +530,11 @@ hjlo_status hjlo_batch_autotune(hjlo_batch *b, const void *const *u, const doubl
     if (s == HJLO_OK) s = trial(&ms1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaStreamSynchronize(b->stream);
+    e = cudaStreamSynchronize(b->stream);
     cudaFree(scratch);
     b->steps = steps0;
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_counters, saved, sizeof(saved), cudaMemcpyHostToDevice);
+    if (s == HJLO_OK && e != cudaSuccess) s = cuda_error(e, "autotune counter restore");
     if (s != HJLO_OK) return s;
     if (!order.empty()) {
         const Group &g = b->groups[order[0]];
@@ -603,6 +610,7 @@ hjlo_status hjlo_batch_sync(hjlo_batch *b, hjlo_counters *out)
         memset(out, 0, sizeof(*out));
         out->exact_rescans = (int64_t)c[CNT_RESCAN];
         out->brute_fallback_lines = (int64_t)c[CNT_FALLBACK];
+        out->window_edge_hits = (int64_t)c[CNT_EDGE];
         out->steps = b->steps;
         out->error_flags = flags;
     }

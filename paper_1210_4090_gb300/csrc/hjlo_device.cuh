@@ -47,7 +47,7 @@ namespace hjlo {
 enum { LAYOUT_CONTIG = 0, LAYOUT_STRIDED = 1 };
 enum { KALGO_BRUTE = 1, KALGO_MONGE = 2, KALGO_DECOMP = 3 };
 enum { FLAG_PRECOND = 1, FLAG_TIMEOUT = 2 };
-enum { CNT_RESCAN = 0, CNT_FALLBACK = 1, CNT_COMPONENTS = 2, CNT_N = 4 };
+enum { CNT_RESCAN = 0, CNT_FALLBACK = 1, CNT_COMPONENTS = 2, CNT_EDGE = 3, CNT_N = 4 };
 
 struct PassParams {
     const void *src;          // tile source (global)
@@ -81,6 +81,7 @@ struct PassParams {
     int hv_scaled;            // 0: hv already holds h*V
     int wide_mul, wide_add;   // MONGE: a bracket of more than wide_mul * (expected span) + wide_add
                               // offsets is searched by the whole warp
+    int edge;                 // partial window: count argmins on its first or last displacement
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -478,19 +479,33 @@ __device__ __forceinline__ int row_or_offload(const PassParams &p, const T *su, 
 
 // ------------------------------------------------------------------ the pass kernel
 
+// 1 when offset t is the first or last of the window (t = 0 or weff - 1).
+__device__ __forceinline__ int on_edge(int t, int weff) { return (unsigned)(t - 1) >= (unsigned)(weff - 2) ? 1 : 0; }
+
+// Adds the threads' window-edge argmins of this tile to the plan's counter;
+// every lane of the warp must call it.
+__device__ __forceinline__ void count_edges(const PassParams &p, int edges)
+{
+    if (!p.edge) return;
+    const int we = __reduce_add_sync(0xffffffffu, edges);
+    if ((threadIdx.x & 31) == 0 && we) atomicAdd(&p.counters[CNT_EDGE], (unsigned long long)we);
+}
+
 // Write-back of rows i = i0, i0 + step, ... < i1 of one contiguous line: the
 // exact value fl(u[src] + k[d]) at the recorded argmin, minus fl(h V) when
 // the pass carries the potential term, stored (binary32: rounded), with the
 // optional argmin.  Four rows per thread at a time, their potential-term
-// loads issued together.
+// loads issued together.  Returns how many of the rows' argmins sit on the
+// window's edge.
 template <typename T>
-__device__ __forceinline__ void write_rows_contig(const PassParams &p, const T *lu, const unsigned short *lt,
+__device__ __forceinline__ int write_rows_contig(const PassParams &p, const T *lu, const unsigned short *lt,
                                                   const double *kr64, T *dst, long long xb, int i0, int i1, int step)
 {
     const int N = (int)p.N;
     T *gd = dst + xb;
     const double *gh = p.hv ? p.hv + xb : nullptr;
     int32_t *ga = p.amin ? p.amin + xb : nullptr;
+    int edges = 0;
     int i = i0;
     for (; i + 3 * step < i1; i += 4 * step) {
         double hvb[4];
@@ -505,6 +520,7 @@ __device__ __forceinline__ void write_rows_contig(const PassParams &p, const T *
             if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, hvb[b]) : hvb[b]);
             store_val(gd + ii, m);
             if (ga) ga[ii] = p.dhi - t;
+            edges += on_edge(t, p.weff);
         }
     }
     for (; i < i1; i += step) {
@@ -514,7 +530,9 @@ __device__ __forceinline__ void write_rows_contig(const PassParams &p, const T *
         if (gh) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, gh[i]) : gh[i]);
         store_val(gd + i, m);
         if (ga) ga[i] = p.dhi - t;
+        edges += on_edge(t, p.weff);
     }
+    return edges;
 }
 
 // Per-line facts of the fixed-point screen, in shared memory.
@@ -846,6 +864,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             __syncwarp();
             T *dst = reinterpret_cast<T *>(p.dst);
             const int nl = (lpl >= 32) ? 1 : (32 >> p.log2lpl);     // lines held by this warp
+            int edges = 0;
             for (int k = 0; k < nl; ++k) {
                 int l = cl, r0 = 0, r1 = N;
                 if (lpl >= 32) {
@@ -856,9 +875,10 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                     l = ((warp << 5) >> p.log2lpl) + k;
                 }
                 if (l >= tl.valid) continue;
-                write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride, r0 + lane, r1,
-                                     32);
+                edges += write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride,
+                                              r0 + lane, r1, 32);
             }
+            count_edges(p, edges);
             return;
         }
     } else {
@@ -896,11 +916,13 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
 
     // ---- exact values, potential term, stores (coalesced order)
     T *dst = reinterpret_cast<T *>(p.dst);
+    int edges = 0;
     if (LAYOUT == LAYOUT_CONTIG) {
         const int lanes = nthr >> p.log2C;              // threads per line
         const int l = tid / lanes, sub = tid - l * lanes;
         if (l < tl.valid)
-            write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride, sub, N, lanes);
+            edges = write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride, sub, N,
+                                         lanes);
     } else {
         const int l = tid & (C - 1);
         if (l < tl.valid) {
@@ -917,9 +939,11 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 if (p.hv) m = __dsub_rn(m, p.hv_scaled ? __dmul_rn(p.hscale, p.hv[x]) : p.hv[x]);
                 store_val(dst + x, m);
                 if (p.amin) p.amin[x] = p.dhi - t;
+                edges += on_edge(t, p.weff);
             }
         }
     }
+    count_edges(p, edges);
 }
 
 template <typename T, int LAYOUT, int ALGO>

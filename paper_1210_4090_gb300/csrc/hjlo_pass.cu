@@ -466,6 +466,7 @@ static void fill_params(const AxisPlan &ax, PassParams &p)
     p.test_extra_tx = ax.test_extra_tx;
     p.wide_mul = ax.wide_mul;
     p.wide_add = ax.wide_add;
+    p.edge = (ax.weff < ax.N) ? 1 : 0;     // full torus windows have no edge
 }
 
 hjlo_status dmalloc(void **ptr, size_t bytes, const char *what)

@@ -42,7 +42,8 @@ class Facts(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [("exact_rescans", _i64), ("brute_fallback_lines", _i64), ("steps", _i64),
-                ("error_flags", _i32), ("reserved", _i32), ("components", _i64)]
+                ("error_flags", _i32), ("reserved", _i32), ("components", _i64),
+                ("window_edge_hits", _i64)]
 
 
 class TuneReport(ctypes.Structure):
@@ -321,7 +322,8 @@ class Plan:
         c = Counters()
         st = lib().hjlo_sync(self._h, ctypes.byref(c))
         res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
-               "steps": c.steps, "error_flags": c.error_flags, "components": c.components}
+               "steps": c.steps, "error_flags": c.error_flags, "components": c.components,
+               "window_edge_hits": c.window_edge_hits}
         _check(st, "hjlo_sync")
         return res
 
@@ -399,7 +401,7 @@ class Batch:
         c = Counters()
         st = lib().hjlo_batch_sync(self._h, ctypes.byref(c))
         res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
-               "steps": c.steps, "error_flags": c.error_flags}
+               "steps": c.steps, "error_flags": c.error_flags, "window_edge_hits": c.window_edge_hits}
         _check(st, "hjlo_batch_sync")
         return res
 

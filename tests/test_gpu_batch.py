@@ -40,12 +40,15 @@ def _run_batch(probs, nsteps, dtype="f64", algo=0):
 @pytest.mark.gpu
 @pytest.mark.parametrize("algo", [1, 2], ids=["brute", "monge"])
 def test_batch_bitwise_vs_oracle(algo):
+    from edge_counts import edge_hits
     probs = _problems(12)
     b, us, _, cnt = _run_batch(probs, 20, algo=algo)
     assert b.groups() >= 2 and cnt["error_flags"] == 0 and cnt["steps"] == 20
     for p, u in zip(probs, us):
         ref = O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, 20)
         assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64)), p.name
+    # window-edge argmins, all instances together
+    assert cnt["window_edge_hits"] == sum(edge_hits(p.u0, p.dx, p.h, p.P, p.W, p.V, 20) for p in probs)
     b.close()
 
 

@@ -52,3 +52,6 @@ def test_random_geometry(i):
     got = u.cpu().numpy()
     view = np.int32 if f32 else np.int64
     assert np.array_equal(got.view(view), ref.view(view)), (shape, W, P, algo, f32)
+    if algo != 3:
+        from edge_counts import edge_hits
+        assert cnt["window_edge_hits"] == edge_hits(u0, dx, h, P, W, V, n)

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from edge_counts import edge_hits
 from paper_1210_4090_gb300 import workloads as WL
 
 torch = pytest.importorskip("torch")
@@ -112,6 +113,19 @@ def test_argmins_exact(case):
         got, am, _ = gpu_run(shape, dx, h, P, W, u0, V, n, algo=algo, argmin=True)
         assert np.array_equal(got.view(np.int64), ref.view(np.int64))
         assert np.array_equal(am, ref_am)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_window_edge_hits(case):
+    """The plan's window_edge_hits counter equals the count taken from the
+    oracle's argmins, for both searches (0 for full torus windows)."""
+    name, shape, dx, h, P, W, n, kind = case
+    u0, V = _data(case)
+    n = min(n, 4)
+    want = edge_hits(u0, dx, h, P, W, V, n)
+    for algo in (1, 2):
+        _, _, cnt = gpu_run(shape, dx, h, P, W, u0, V, n, algo=algo)
+        assert cnt["window_edge_hits"] == want, (name, algo, cnt, want)
 
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] in
