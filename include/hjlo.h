@@ -97,6 +97,11 @@ typedef struct {
     double kmin[HJLO_MAX_DIM];    /* min_d k_a[d] */
     double curvature[HJLO_MAX_DIM]; /* min second difference of the k_a table */
     int64_t npts;                 /* prod(shape) */
+    int64_t row_blocks[HJLO_MAX_DIM]; /* 1: each CTA stages whole lines of axis a; k > 1: every
+                                     line of the contiguous axis is cut into k blocks of rows,
+                                     each staged with the window span it needs (lines longer
+                                     than one CTA's shared memory, or too few lines to fill
+                                     the GPU; windows up to a quarter of the line) */
 } hjlo_plan_facts;
 
 /* Device-side counters of a plan (host struct filled by hjlo_sync). */

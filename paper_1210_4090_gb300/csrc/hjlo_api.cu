@@ -331,6 +331,7 @@ hjlo_status hjlo_plan_info(const hjlo_plan *p, hjlo_plan_facts *info)
         info->centre[a] = p->ax[a].centre;
         info->kmin[a] = p->ax[a].kmin;
         info->curvature[a] = p->ax[a].curv;
+        info->row_blocks[a] = p->ax[a].vblocks;
     }
     return HJLO_OK;
 }

@@ -311,11 +311,13 @@ hjlo_status hjlo_batch_create(const hjlo_desc *descs, int32_t count, void *cuda_
         const int rep = g.members[0];
         for (int a = 0; a < b->ndim && s == HJLO_OK; ++a) {
             AxisPlan ax = b->inst[(size_t)rep * b->ndim + a];
-            s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size(), nullptr);
+            s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size(), nullptr,
+                             false);
             if (s == HJLO_EUNSUPPORTED && ax.algo == KALGO_MONGE && b->descs[rep].algo == HJLO_ALGO_AUTO) {
                 // lines too long for the monotone search's shared memory
                 ax.algo = KALGO_BRUTE;
-                s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size());
+                s = shape_launch(ax, b->esize, ax.algo, df.num_sms, df.smem_optin, (long long)g.members.size(), nullptr,
+                                 false);
             }
             if (s != HJLO_OK) break;
             apply_group_shape(b, g, a, ax);
@@ -506,7 +508,7 @@ hjlo_status hjlo_batch_autotune(hjlo_batch *b, const void *const *u, const doubl
             for (const ShapeHints &h : tune_candidates(start)) {
                 AxisPlan t = start;
                 if (shape_launch(t, b->esize, KALGO_MONGE, df.num_sms, df.smem_optin, (long long)g.members.size(),
-                                 &h) != HJLO_OK)
+                                 &h, false) != HJLO_OK)
                     continue;
                 if (t.lpl == best.lpl && t.C == best.C && t.wide_mul == best.wide_mul && t.wide_add == best.wide_add)
                     continue;

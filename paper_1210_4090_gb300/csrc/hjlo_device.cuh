@@ -82,7 +82,27 @@ struct PassParams {
     int wide_mul, wide_add;   // MONGE: a bracket of more than wide_mul * (expected span) + wide_add
                               // offsets is searched by the whole warp
     int edge;                 // partial window: count argmins on its first or last displacement
+    // Row blocks (contiguous lines only; vN = 0 otherwise).  A line of vN points
+    // is cut into vblocks blocks of vR rows; block b of real line rl is the
+    // tile line rl * vblocks + b, staged as a periodic line of N = vR + weff - 1
+    // points: halo index jj <-> real position (b * vR + jj + vhoff) mod vN.
+    // Its first vR rows see no wrap, so their minima are the real rows'.
+    long long vN, vblocks;
+    int vR, vhoff;
 };
+
+// Real line, first row and row count of tile line vl in row-block mode.
+struct RowBlock {
+    long long base;   // global index of the block's first row
+    int rows;         // real rows of the block
+};
+__device__ __forceinline__ RowBlock row_block(const PassParams &p, long long vl)
+{
+    const long long rl = vl / p.vblocks;
+    const long long r0 = (vl - rl * p.vblocks) * p.vR;
+    const long long left = p.vN - r0;
+    return RowBlock{rl * p.vN + r0, (int)(left < p.vR ? left : p.vR)};
+}
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -590,6 +610,20 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                     tma_tensor_load_3d(su + (long long)b * p.by * C, tmap, x0, b * p.by, (int)o, bar);
             }
         }
+    } else if (LAYOUT == LAYOUT_CONTIG && p.vN) {
+        // row blocks: gather each block's window span from its real line
+        // (N <= vN, so one wrap at most)
+        for (int l = 0; l < tl.valid; ++l) {
+            const long long vl = (tile << p.log2C) + l;
+            const long long rl = vl / p.vblocks;
+            const T *ls = src + rl * p.vN;
+            const long long s0 = ((vl - rl * p.vblocks) * p.vR + p.vhoff) % p.vN;
+            for (int i = tid; i < N; i += nthr) {
+                long long q = s0 + i;
+                q = (q >= p.vN) ? q - p.vN : q;
+                su[l * N + i] = ls[q];
+            }
+        }
     } else {
         for (int l = 0; l < tl.valid; ++l)
             for (int i = tid; i < N; i += nthr)
@@ -597,7 +631,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     }
     // the potential term of a contiguous tile is read at the very end: start
     // moving it towards L2 now, behind the search
-    if (LAYOUT == LAYOUT_CONTIG && p.hv && tid == nthr - 1)
+    if (LAYOUT == LAYOUT_CONTIG && p.hv && !p.vN && tid == nthr - 1)
         prefetch_l2(p.hv + tl.base, (unsigned long long)tl.valid * N * sizeof(double));
     for (int i = tid; i < weff; i += nthr) kr64[i] = p.kr64[i];
     if (p.use_tma) {
@@ -875,8 +909,13 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                     l = ((warp << 5) >> p.log2lpl) + k;
                 }
                 if (l >= tl.valid) continue;
-                edges += write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride,
-                                              r0 + lane, r1, 32);
+                long long xb = tl.base + l * tl.lstride;
+                if (p.vN) {
+                    const RowBlock rb = row_block(p, (tile << p.log2C) + l);
+                    xb = rb.base;
+                    r1 = min(r1, rb.rows);
+                }
+                edges += write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, xb, r0 + lane, r1, 32);
             }
             count_edges(p, edges);
             return;
@@ -920,9 +959,16 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     if (LAYOUT == LAYOUT_CONTIG) {
         const int lanes = nthr >> p.log2C;              // threads per line
         const int l = tid / lanes, sub = tid - l * lanes;
-        if (l < tl.valid)
-            edges = write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, tl.base + l * tl.lstride, sub, N,
-                                         lanes);
+        if (l < tl.valid) {
+            long long xb = tl.base + l * tl.lstride;
+            int rows = N;
+            if (p.vN) {
+                const RowBlock rb = row_block(p, (tile << p.log2C) + l);
+                xb = rb.base;
+                rows = rb.rows;
+            }
+            edges = write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, xb, sub, rows, lanes);
+        }
     } else {
         const int l = tid & (C - 1);
         if (l < tl.valid) {

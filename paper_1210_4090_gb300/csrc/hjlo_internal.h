@@ -30,6 +30,11 @@ struct AxisPlan {
     int test_extra_tx = 0;                 // test knob, see apply_test_knobs
     int wide_mul = 2, wide_add = 8;        // warp offload of wide brackets (see PassParams)
     double eta = 0.0;                      // DECOMP: convexity tolerance of the decomposition
+    // row blocks of a contiguous axis (vblocks > 1): each line is cut into
+    // vblocks blocks of vR rows, each launched as a line of vNp = vR + weff - 1
+    // points (see PassParams); the launch fields below then describe those
+    long long vblocks = 1, vNp = 0;
+    int vR = 0;
     int by = 1, nbox = 1, lp = 0;
     long long ntiles = 0, tiles_per_outer = 1;
     size_t smem = 0;
@@ -60,8 +65,10 @@ ShapeHints env_hints();
 // Chooses lines per tile, lanes per line and shared-memory layout; `replicas`
 // grids of this shape run in the same launch (batched passes).  `hints`
 // (null: the environment's) override the cost model where they are valid.
+// `row_blocks`: a contiguous axis may be launched as row blocks (single
+// grids only; the batched kernel launches whole lines).
 hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
-                         long long replicas = 1, const ShapeHints *hints = nullptr);
+                         long long replicas = 1, const ShapeHints *hints = nullptr, bool row_blocks = true);
 
 // Candidate shapes around ax's current one for the autotuner: lanes per line
 // and lines per tile halved / kept / doubled, offload on / off.

@@ -226,8 +226,65 @@ std::vector<ShapeHints> tune_candidates(const AxisPlan &ax)
     return out;
 }
 
+static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
+                               long long replicas, const ShapeHints *hints);
+
+// Rows per block for a contiguous axis, or 0 to launch whole lines.  Blocks
+// are used when the window is at most a quarter of the line and either a
+// whole line does not fit in one CTA's shared memory or the axis has fewer
+// lines than half the SMs; they hold about one SM's share of the rows, at
+// least 2 (weff - 1) (a block stages vR + weff - 1 points for vR rows) and
+// at most what fits.
+static long long block_rows(const AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin)
+{
+    const long long N = ax.N, w = ax.weff, lines = ax.outer;
+    if (ax.inner != 1 || 4 * w > N) return 0;
+    // shared memory per staged point and per window entry (layout_smem)
+    const long long per_pt = esize + 2 + ((algo == KALGO_MONGE) ? 4 : 0);
+    const long long per_w = 8 + ((algo == KALGO_MONGE) ? 8 : 0);
+    const long long room = (long long)smem_optin - 1024 - per_w * w;
+    const long long fit_pts = room > 0 ? room / per_pt : 0;         // staged points that fit
+    const bool fits = N + w <= fit_pts;
+    if (fits && 2 * lines >= num_sms) return 0;
+    long long vR = std::max(2 * (w - 1), (N * lines + num_sms - 1) / num_sms);
+    vR = std::min(vR, fit_pts - (w - 1));
+    vR = std::min(vR, N - (w - 1));                                 // a block never spans the line
+    if (vR < std::max(1LL, w - 1) || vR >= N) return 0;
+    return vR;
+}
+
 hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin, long long replicas,
-                         const ShapeHints *hints)
+                         const ShapeHints *hints, bool row_blocks)
+{
+    ax.vblocks = 1;
+    ax.vR = 0;
+    ax.vNp = 0;
+    if ((algo == KALGO_MONGE || algo == KALGO_BRUTE) && row_blocks) {
+        const long long vR = block_rows(ax, esize, algo, num_sms, smem_optin);
+        if (vR > 0) {
+            AxisPlan v = ax;
+            v.N = vR + ax.weff - 1;
+            v.vblocks = (ax.N + vR - 1) / vR;
+            v.outer = ax.outer * v.vblocks;
+            v.hoff = 0;
+            hjlo_status s = shape_lines(v, esize, algo, num_sms, smem_optin, 1, hints);
+            if (s != HJLO_OK) return s;
+            // launch fields from the block lines; geometry and tables stay the axis's
+            AxisPlan r = v;
+            r.N = ax.N;
+            r.outer = ax.outer;
+            r.hoff = ax.hoff;
+            r.vR = (int)vR;
+            r.vNp = v.N;
+            ax = r;
+            return HJLO_OK;
+        }
+    }
+    return shape_lines(ax, esize, algo, num_sms, smem_optin, replicas, hints);
+}
+
+static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
+                               long long replicas, const ShapeHints *hints)
 {
     const ShapeHints hint = hints ? *hints : env_hints();
     ax.algo = algo;
@@ -467,6 +524,15 @@ static void fill_params(const AxisPlan &ax, PassParams &p)
     p.wide_mul = ax.wide_mul;
     p.wide_add = ax.wide_add;
     p.edge = (ax.weff < ax.N) ? 1 : 0;     // full torus windows have no edge
+    if (ax.vblocks > 1) {
+        p.N = ax.vNp;
+        p.outer = ax.outer * ax.vblocks;
+        p.hoff = 0;
+        p.vN = ax.N;
+        p.vblocks = ax.vblocks;
+        p.vR = ax.vR;
+        p.vhoff = ax.hoff;
+    }
 }
 
 hjlo_status dmalloc(void **ptr, size_t bytes, const char *what)
@@ -520,7 +586,7 @@ hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *ds
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     if (ax.layout == LAYOUT_CONTIG) {
-        p.use_tma = (((uintptr_t)src & 15) == 0) && (((ax.N * esize) & 15) == 0);
+        p.use_tma = (ax.vblocks == 1) && (((uintptr_t)src & 15) == 0) && (((ax.N * esize) & 15) == 0);
     } else {
         p.use_tma = encode_strided(ax, esize, src, &map) ? 1 : 0;
     }

@@ -21,14 +21,16 @@ def test_bitwise_vs_oracle(law, K):
     assert np.array_equal(got.view(np.int64), ref.view(np.int64))
 
 
-def test_long_line_falls_back_to_brute_force():
-    """2 x 8192 points do not fit the monotone search's shared-memory layout;
-    the library's automatic choice takes brute force for them, still exact."""
+def test_long_line_runs_in_row_blocks():
+    """2 x 8192 points on one line: the monotone search runs it as blocks of
+    rows spread over the GPU (a whole line would not fit one CTA's shared
+    memory), still exact."""
     from paper_1210_4090_gb300 import hjlo
     p = E.LAWS["tdep"](8192)
     n = 4
     plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W)
-    assert plan.info()["algo"] == "brute"
+    info = plan.info()
+    assert info["algo"] == "monge" and info["row_blocks"][0] > 1, info
     u = torch.tensor(p.u0, device="cuda")
     plan.run_tv(u, torch.tensor(p.V[:n], device="cuda"), n)
     plan.close()
