@@ -38,6 +38,24 @@ def test_long_line_runs_in_row_blocks():
     assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64))
 
 
+def test_paper_size_pendulum_line():
+    """The paper's largest run (Sec. 5.1 footnote): 2^18 points, tau = sqrt(dx),
+    one line in row blocks; the first steps bit-exact against the oracle."""
+    from paper_1210_4090_gb300 import hjlo
+    p = E.LAWS["pendulum"](2 ** 17)
+    n = 2
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W)
+    info = plan.info()
+    assert info["algo"] == "monge" and info["row_blocks"][0] > 1, info
+    u = torch.tensor(p.u0, device="cuda")
+    plan.run(u, torch.tensor(p.V, device="cuda"), n)
+    cnt = plan.sync()
+    plan.close()
+    assert cnt["error_flags"] == 0 and cnt["window_edge_hits"] == 0
+    ref = O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, n)
+    assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64))
+
+
 @pytest.mark.parametrize("law", ["pendulum", "tdep"])
 def test_order_one_half_on_gpu(law):
     r = E.convergence(law, [16, 32, 64, 128, 256, 512, 1024], 4096)
