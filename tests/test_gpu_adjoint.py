@@ -3,10 +3,10 @@
 dJ/du0 and dJ/dV are summed in the definition's order (ascending target per
 source, reverse steps), so they must equal the oracle's bit for bit; dJ/dP is
 a global sum in another order (rtol 1e-11).  Cases: 1D/2D/3D, windowed and
-full windows, several checkpoint intervals, the adjoint512 law on a 64^2 copy
-with the 64 coefficient gradients, |u| ~ 1e14 (non-monotone argmins take the
-sequential path), finite differences through the forward kernels, and the
-torch.autograd binding.
+full windows, contiguous axes in row blocks, several checkpoint intervals,
+the adjoint512 law on a 64^2 copy with the 64 coefficient gradients,
+|u| ~ 1e14 (non-monotone argmins take the sequential path), finite
+differences through the forward kernels, and the torch.autograd binding.
 """
 import numpy as np
 import pytest
@@ -37,7 +37,9 @@ def _gpu_adjoint(shape, dx, h, P, W, u0, V, n, ub, S):
     return g0.cpu().numpy(), gP.cpu().numpy(), None if gV is None else gV.cpu().numpy(), un.cpu().numpy(), cnt
 
 
-CASES = [((40,), (0,), 9), ((24, 30), (4, 5), 7), ((9, 10, 12), (2, 0, 3), 5), ((33, 18), (0, 3), 6)]
+# the last two run their contiguous axis in row blocks (one or three lines)
+CASES = [((40,), (0,), 9), ((24, 30), (4, 5), 7), ((9, 10, 12), (2, 0, 3), 5), ((33, 18), (0, 3), 6),
+         ((300,), (12,), 6), ((3, 200), (1, 10), 5)]
 
 
 @pytest.mark.parametrize("shape,W,n", CASES, ids=lambda c: str(c))
