@@ -130,8 +130,13 @@ typedef struct {
  * searched in a narrow range bracketed by its neighbours' argmins.  The plan
  * checks that the table's second differences are positive; each launch
  * re-checks the rounding margin per line and falls back to brute force for a
- * line that fails it (counted in hjlo_counters).  Under HJLO_ALGO_AUTO a line
- * too long for the monotone search's shared-memory layout takes brute force.
+ * line that fails it (counted in hjlo_counters).  A contiguous axis whose
+ * lines are longer than one CTA's shared memory holds, or too few to fill the
+ * GPU, is launched in blocks of rows when its window is at most a quarter of
+ * the line: each block is staged with the window span its rows need, so the
+ * results are those of whole lines (hjlo_plan_facts.row_blocks).  Other lines
+ * too long for the monotone search (full or wide windows, strided axes) take
+ * brute force under HJLO_ALGO_AUTO where that fits.
  * HJLO_ALGO_DECOMP runs every pass by the paper's own method (Sec. 4): each
  * line is cut into convex and concave components (tolerance eta, Sec. 4.4,
  * default 0), each is convolved with the convex kernel in linear time
@@ -142,8 +147,8 @@ typedef struct {
  * (HJLO_EPRECOND otherwise) and records no argmins (hjlo_step with
  * argmin_out and hjlo_adjoint return HJLO_EUNSUPPORTED).
  * Errors: HJLO_EINVAL (bad descriptor), HJLO_EUNSUPPORTED (a line of the grid
- * does not fit in one CTA's shared memory), HJLO_EPRECOND, HJLO_ENOMEM,
- * HJLO_ECUDA.
+ * does not fit in one CTA's shared memory and cannot run in row blocks),
+ * HJLO_EPRECOND, HJLO_ENOMEM, HJLO_ECUDA.
  */
 hjlo_status hjlo_plan_create(const hjlo_desc *desc, void *cuda_stream, hjlo_plan **out);
 
