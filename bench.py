@@ -496,12 +496,13 @@ def run_paper1d(args):
     tdep = {"shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W), "ms": ms_tv,
             "value": p.npts * p.nsteps / (ms_tv * 1e-3), "row_blocks": plan.info()["row_blocks"]}
     plan.close()
-    # the paper's timed run
+    # the paper's timed run (launch shapes tuned first, outside the timed region)
     q = WL.pendulum(2 ** 17)
     plan = hjlo.Plan(q.shape, q.dx, q.h, q.P, q.W)
+    qu0, qV = torch.tensor(q.u0, device=dev), torch.tensor(q.V, device=dev)
+    tune = None if args.no_autotune else plan.autotune(qu0, qV, 16)
     info = plan.info()
-    ms, u = _time_run(plan, torch.tensor(q.u0, device=dev), torch.tensor(q.V, device=dev), q.nsteps,
-                      args.steps, args.warmup)
+    ms, u = _time_run(plan, qu0, qV, q.nsteps, args.steps, args.warmup)
     cnt = plan.sync()
     plan.close()
     updates = q.npts * q.nsteps
@@ -511,6 +512,7 @@ def run_paper1d(args):
             "data": "synthetic (deterministic: the paper's Sec. 5 laws)",
             "config": {"workload": "pendulum_2^18", "shape": list(q.shape), "nsteps": q.nsteps, "W": list(q.W),
                        "h": q.h, "P": list(q.P), "T": q.extra["T"], "row_blocks": info["row_blocks"],
+                       "autotune": tune,
                        "paper_context": "~19 min (1140 s) in MATLAB on a 2.3 GHz laptop core with the "
                                         "approximate decomposition method (eta = dx): another method and "
                                         "machine, not a target"},

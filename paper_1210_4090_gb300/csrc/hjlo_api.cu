@@ -486,7 +486,8 @@ hjlo_status hjlo_plan_autotune(hjlo_plan *p, const void *u, const double *V, int
         for (const ShapeHints &h : tune_candidates(p->ax[a])) {
             AxisPlan t = p->ax[a];
             if (shape_launch(t, p->esize, KALGO_MONGE, df.num_sms, df.smem_optin, 1, &h) != HJLO_OK) continue;
-            if (t.lpl == best.lpl && t.C == best.C && t.wide_mul == best.wide_mul && t.wide_add == best.wide_add)
+            if (t.lpl == best.lpl && t.C == best.C && t.wide_mul == best.wide_mul && t.wide_add == best.wide_add &&
+                t.vR == best.vR)
                 continue;
             AxisPlan keep = p->ax[a];
             p->ax[a] = t;

@@ -56,10 +56,11 @@ struct ShapeHints {
     int C = 0;                   // lines per tile (power of two)
     int wide_mul = -1;           // offload rule of wide brackets (wide_mul, wide_add);
     int wide_add = -1;           // wide_mul = 0 with a huge wide_add turns it off
+    long long block_rows = 0;    // rows per row block of a contiguous axis (0: cost model)
 };
 
 // The tuning overrides of the environment (HJLO_LANES_PER_LINE,
-// HJLO_LINES_PER_TILE, HJLO_OFFLOAD) as hints.
+// HJLO_LINES_PER_TILE, HJLO_OFFLOAD, HJLO_BLOCK_ROWS) as hints.
 ShapeHints env_hints();
 
 // Chooses lines per tile, lanes per line and shared-memory layout; `replicas`

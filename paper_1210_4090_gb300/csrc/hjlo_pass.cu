@@ -191,6 +191,7 @@ ShapeHints env_hints()
     ShapeHints h;
     if (const char *e = getenv("HJLO_LANES_PER_LINE")) h.lpl = atoi(e);
     if (const char *e = getenv("HJLO_LINES_PER_TILE")) h.C = atoi(e);
+    if (const char *e = getenv("HJLO_BLOCK_ROWS")) h.block_rows = atoll(e);
     if (const char *e = getenv("HJLO_OFFLOAD")) {
         int m = 0, a = 0;
         if (sscanf(e, "%d,%d", &m, &a) == 2 && m >= 0 && a >= 0) {
@@ -209,17 +210,26 @@ std::vector<ShapeHints> tune_candidates(const AxisPlan &ax)
     std::vector<ShapeHints> out;
     const int lpls[3] = {ax.lpl / 2, ax.lpl, ax.lpl * 2};
     const int Cs[3] = {ax.C / 2, ax.C, ax.C * 2};
-    for (int li = 0; li < 3; ++li) {
-        if (lpls[li] < 1 || lpls[li] > 1024 || lpls[li] > ax.N) continue;
-        for (int ci = 0; ci < 3; ++ci) {
-            if (Cs[ci] < 1) continue;
-            for (int off = 0; off < 2; ++off) {
-                ShapeHints h;
-                h.lpl = lpls[li];
-                h.C = Cs[ci];
-                h.wide_mul = off ? 0 : 2;
-                h.wide_add = off ? (1 << 24) : 8;
-                out.push_back(h);
+    // row-block axes: rows per block halved / kept / doubled as well
+    const long long vRs[3] = {ax.vR / 2, (long long)ax.vR, 2LL * ax.vR};
+    const int nb = (ax.vblocks > 1) ? 3 : 1;
+    const long long line = (ax.vblocks > 1) ? ax.vNp : ax.N;
+    for (int bi = 0; bi < nb; ++bi) {
+        const long long br = (nb == 3) ? vRs[bi] : 0;
+        if (nb == 3 && br < 1) continue;
+        for (int li = 0; li < 3; ++li) {
+            if (lpls[li] < 1 || lpls[li] > 1024 || lpls[li] > line) continue;
+            for (int ci = 0; ci < 3; ++ci) {
+                if (Cs[ci] < 1) continue;
+                for (int off = 0; off < 2; ++off) {
+                    ShapeHints h;
+                    h.lpl = lpls[li];
+                    h.C = Cs[ci];
+                    h.wide_mul = off ? 0 : 2;
+                    h.wide_add = off ? (1 << 24) : 8;
+                    h.block_rows = br;
+                    out.push_back(h);
+                }
             }
         }
     }
@@ -234,8 +244,10 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
 // whole line does not fit in one CTA's shared memory or the axis has fewer
 // lines than half the SMs; they hold about one SM's share of the rows, at
 // least 2 (weff - 1) (a block stages vR + weff - 1 points for vR rows) and
-// at most what fits.
-static long long block_rows(const AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin)
+// at most what fits.  A hint (hinted > 0) replaces the share, within
+// [weff - 1, what fits].
+static long long block_rows(const AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
+                            long long hinted)
 {
     const long long N = ax.N, w = ax.weff, lines = ax.outer;
     if (ax.inner != 1 || 4 * w > N) return 0;
@@ -247,6 +259,7 @@ static long long block_rows(const AxisPlan &ax, int esize, int algo, int num_sms
     const bool fits = N + w <= fit_pts;
     if (fits && 2 * lines >= num_sms) return 0;
     long long vR = std::max(2 * (w - 1), (N * lines + num_sms - 1) / num_sms);
+    if (hinted > 0) vR = std::max(hinted, std::max(1LL, w - 1));
     vR = std::min(vR, fit_pts - (w - 1));
     vR = std::min(vR, N - (w - 1));                                 // a block never spans the line
     if (vR < std::max(1LL, w - 1) || vR >= N) return 0;
@@ -260,7 +273,8 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
     ax.vR = 0;
     ax.vNp = 0;
     if ((algo == KALGO_MONGE || algo == KALGO_BRUTE) && row_blocks) {
-        const long long vR = block_rows(ax, esize, algo, num_sms, smem_optin);
+        const ShapeHints hint = hints ? *hints : env_hints();
+        const long long vR = block_rows(ax, esize, algo, num_sms, smem_optin, hint.block_rows);
         if (vR > 0) {
             AxisPlan v = ax;
             v.N = vR + ax.weff - 1;

@@ -73,3 +73,30 @@ def test_autotune_binary32_storage():
     ref = O.run(u0, p.dx, p.h, p.P, p.W, p.V, 20)
     assert np.array_equal(u.cpu().numpy().view(np.int32), ref.view(np.int32))
     plan.close()
+
+
+def test_autotune_row_blocks():
+    """A single 1D line in row blocks: the tuner also varies the rows per
+    block; whatever it keeps, the run stays bit-exact, the counters are the
+    run's own (trials leave them untouched) and the data is untouched."""
+    from paper_1210_4090_gb300 import hjlo
+    from edge_counts import edge_hits
+    N, W, h, P, n = 20000, 30, 1e-4, 0.2, 3
+    x = np.arange(N) / N
+    rng = np.random.default_rng(12)
+    u0 = 0.3 * np.sin(6 * np.pi * x) + 0.01 * rng.normal(size=N)
+    V = 0.2 * np.cos(4 * np.pi * x)
+    plan = hjlo.Plan((N,), 1.0 / N, h, P, W)
+    assert plan.info()["row_blocks"][0] > 1
+    u = torch.tensor(u0, device="cuda")
+    Vt = torch.tensor(V, device="cuda")
+    before = u.clone()
+    rep = plan.autotune(u, Vt, 4)
+    assert torch.equal(u, before) and rep["trials"] >= 3
+    assert plan.info()["row_blocks"][0] > 1
+    plan.run(u, Vt, n)
+    cnt = plan.sync()
+    plan.close()
+    ref = O.run(u0, 1.0 / N, h, P, W, V, n)
+    assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64))
+    assert cnt["steps"] == n and cnt["window_edge_hits"] == edge_hits(u0, 1.0 / N, h, P, W, V, n)
