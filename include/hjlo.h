@@ -102,6 +102,8 @@ typedef struct {
                                      each staged with the window span it needs (lines longer
                                      than one CTA's shared memory, or too few lines to fill
                                      the GPU; windows up to a quarter of the line) */
+    int64_t block_rows[HJLO_MAX_DIM]; /* rows per block when row_blocks[a] > 1 (the last block
+                                     holds the rest), else 0 */
 } hjlo_plan_facts;
 
 /* Device-side counters of a plan (host struct filled by hjlo_sync). */

@@ -332,6 +332,7 @@ hjlo_status hjlo_plan_info(const hjlo_plan *p, hjlo_plan_facts *info)
         info->kmin[a] = p->ax[a].kmin;
         info->curvature[a] = p->ax[a].curv;
         info->row_blocks[a] = p->ax[a].vblocks;
+        info->block_rows[a] = (p->ax[a].vblocks > 1) ? p->ax[a].vR : 0;
     }
     return HJLO_OK;
 }

@@ -6,7 +6,8 @@
 // lm:simplif / Theorem th:ccc / Algorithm 2 for a concave one), and the
 // output is the minimum over components (Sec. 4.3 step 3).
 //
-// One CTA per line.  The lifted source line and the kernel are staged in
+// One CTA per line (or row block of a long or lonely contiguous line, each
+// decomposed on its own span).  The lifted source line and the kernel are staged in
 // shared memory; the slope-increment kinds of all interior points are
 // classified in parallel into two bitmaps; one thread walks the bitmaps to
 // cut the components greedily (the cut is a left-to-right dependency chain,
@@ -46,6 +47,10 @@ struct DecompParams {
     int nwords;                  // (L + 31) / 32
     double eta;
     int off_f, off_r, off_keys, off_cv, off_cc, off_comp, off_fm, off_misc;
+    // row blocks (contiguous lines; vN = 0 otherwise): a line of vN points is
+    // cut into vblocks blocks of N rows; block b of real line rl is CTA
+    // rl * vblocks + b, with sources (b N + y + hoff) mod vN, y in [0, L)
+    long long vN, vblocks;
 };
 
 // Candidate v for output x = z - n.  Most candidates lose: a plain read of
@@ -165,12 +170,32 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
     const long long line = blockIdx.x;
-    const long long o = line / p.inner, in = line - o * p.inner;
-    const long long base = o * p.N * p.inner + in, stride = p.inner;
     const int N = (int)p.N, n = p.n, L = p.L;
-
-    // ---- stage: g[y] = u((y - dhi) mod N), f(i) = k[dlo + i]
-    for (int y = tid; y < L; y += nthr) g[y] = p.src[base + (long long)((y + p.hoff) % N) * stride];
+    long long base, stride;
+    int rows = N;                               // outputs written back
+    if (p.vN) {
+        const long long rl = line / p.vblocks;
+        const long long r0 = (line - rl * p.vblocks) * p.N;
+        const long long left = p.vN - r0;
+        rows = (int)(left < p.N ? left : p.N);
+        base = rl * p.vN + r0;
+        stride = 1;
+        // ---- stage the block's span: g[y] = u((r0 + y - dhi) mod vN) (L <= vN: one wrap)
+        const double *ls = p.src + rl * p.vN;
+        const long long q0 = (r0 + p.hoff) % p.vN;
+        for (int y = tid; y < L; y += nthr) {
+            long long q = q0 + y;
+            q = (q >= p.vN) ? q - p.vN : q;
+            g[y] = ls[q];
+        }
+    } else {
+        const long long o = line / p.inner, in = line - o * p.inner;
+        base = o * p.N * p.inner + in;
+        stride = p.inner;
+        // ---- stage: g[y] = u((y - dhi) mod N)
+        for (int y = tid; y < L; y += nthr) g[y] = p.src[base + (long long)((y + p.hoff) % N) * stride];
+    }
+    // f(i) = k[dlo + i]
     for (int i = tid; i <= n; i += nthr) f[i] = p.kr64[n - i];
     for (int x = tid; x < N; x += nthr) keys[x] = ~0ull;
     __syncthreads();
@@ -232,7 +257,7 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     __syncthreads();
 
     // ---- values, potential term, stores
-    for (int x = tid; x < N; x += nthr) {
+    for (int x = tid; x < rows; x += nthr) {
         const unsigned long long k = keys[x];
         if (k == ~0ull) {                  // no component reached x: cannot happen for a convex kernel
             atomicOr(p.flags, FLAG_PRECOND);
@@ -245,9 +270,10 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     }
 }
 
-size_t decomp_smem(const AxisPlan &ax, DecompParams *p)
+// Shared memory of one CTA for lines (or row blocks) of N outputs.
+size_t decomp_smem(const AxisPlan &ax, long long N, DecompParams *p)
 {
-    const long long N = ax.N, n = ax.weff - 1, L = N + n, nwords = (L + 31) / 32;
+    const long long n = ax.weff - 1, L = N + n, nwords = (L + 31) / 32;
     size_t off = 0;
     off += sizeof(double) * L;                                  // g
     const size_t off_f = off;
@@ -295,12 +321,31 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms)
 {
     ax.algo = KALGO_DECOMP;
     ax.layout = (ax.inner == 1) ? LAYOUT_CONTIG : LAYOUT_STRIDED;
-    ax.smem = decomp_smem(ax, nullptr);
-    if (ax.smem > smem_optin || ax.N + ax.weff > (1LL << 30))
-        return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit the decomposition pass", ax.N);
+    ax.vblocks = 1;
+    ax.vR = 0;
+    ax.vNp = 0;
     if (ax.weff >= 3 && !(ax.curv > 0))
         return set_error(HJLO_EPRECOND, "the decomposition pass needs a strictly convex kernel table");
-    ax.ntiles = ax.inner * ax.outer;
+    // Row blocks for a contiguous axis, as for the other passes: when the
+    // window is at most a quarter of the line and either a whole line does
+    // not fit or the axis has fewer lines than half the SMs.  Each block is
+    // decomposed on its own span (the cut restarts at the block's first source).
+    const long long N = ax.N, w = ax.weff, lines = ax.outer;
+    const bool fits = decomp_smem(ax, N, nullptr) <= smem_optin;
+    if (ax.inner == 1 && 4 * w <= N && (!fits || 2 * lines < num_sms)) {
+        long long vR = std::max(2 * (w - 1), (N * lines + num_sms - 1) / num_sms);
+        while (vR > w - 1 && decomp_smem(ax, vR, nullptr) > smem_optin) vR = vR * 3 / 4;
+        vR = std::min(vR, N - (w - 1));                  // span vR + weff - 1 <= N: one wrap
+        if (vR >= std::max(1LL, w - 1) && vR < N && decomp_smem(ax, vR, nullptr) <= smem_optin) {
+            ax.vR = (int)vR;
+            ax.vblocks = (N + vR - 1) / vR;
+        }
+    }
+    const long long rowsN = (ax.vblocks > 1) ? ax.vR : N;
+    ax.smem = decomp_smem(ax, rowsN, nullptr);
+    if (ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))
+        return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit the decomposition pass", ax.N);
+    ax.ntiles = ax.inner * ax.outer * ax.vblocks;
     // one CTA per line: few lines (a 1D problem) get 32 warps each to hide
     // the latency of their components' searches; many lines get 8 warps
     // (measured: 2 x 4096-point pendulum 137 -> 100 ms, 1024^2 law 51 ms at
@@ -317,7 +362,8 @@ hjlo_status launch_decomp(const AxisPlan &ax, const void *src, void *dst, const 
 {
     DecompParams p;
     memset(&p, 0, sizeof(p));
-    decomp_smem(ax, &p);
+    const bool blocks = ax.vblocks > 1;
+    decomp_smem(ax, blocks ? ax.vR : ax.N, &p);
     p.src = reinterpret_cast<const double *>(src);
     p.dst = reinterpret_cast<double *>(dst);
     p.hv = hv;
@@ -326,11 +372,15 @@ hjlo_status launch_decomp(const AxisPlan &ax, const void *src, void *dst, const 
     p.kr64 = ax.d_kr64;
     p.counters = counters;
     p.flags = flags;
-    p.N = ax.N;
+    p.N = blocks ? ax.vR : ax.N;
     p.inner = ax.inner;
     p.outer = ax.outer;
     p.hoff = ax.hoff;
     p.eta = ax.eta;
+    if (blocks) {
+        p.vN = ax.N;
+        p.vblocks = ax.vblocks;
+    }
     decomp_kernel<<<(unsigned)ax.ntiles, ax.threads, ax.smem, st>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "decomposition kernel launch");

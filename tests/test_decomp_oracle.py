@@ -120,3 +120,20 @@ def test_error_grows_with_eta_and_components_shrink():
     assert errs[0] <= 1e-14
     assert comps == sorted(comps, reverse=True) and comps[-1] < comps[0]
     assert errs[-1] >= errs[0]
+
+
+def test_blocks_at_zero_tolerance_equal_the_scheme():
+    """At eta = 0 every component is exactly convex or concave and the method
+    is exact, so restarting the decomposition at each block of rows changes
+    nothing: equal to the scheme (and to the whole-line decomposition)."""
+    N, W, h = 300, 12, 0.01
+    x = np.arange(N) / N
+    rng = np.random.default_rng(5)
+    u0 = 0.3 * np.sin(6 * np.pi * x) + 0.01 * rng.normal(size=N)
+    V = 0.1 * np.cos(2 * np.pi * x)
+    ref = O.run(u0, 1.0 / N, h, 0.2, W, V, 3)
+    for R in (24, 40, 77, 300):
+        got, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, V, 3, 0.0, block_rows=R)
+        assert np.array_equal(got.view(np.int64), ref.view(np.int64)), R
+    whole, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, V, 3, 0.0)
+    assert np.array_equal(whole.view(np.int64), ref.view(np.int64))

@@ -19,10 +19,16 @@ def _hjlo():
     return hjlo
 
 
-def gpu_decomp(shape, dx, h, P, W, u0, V, nsteps, eta=0.0, V_per_step=False):
+def gpu_decomp(shape, dx, h, P, W, u0, V, nsteps, eta=0.0, V_per_step=False, facts=None):
+    """Runs the decomposition pass; `facts`, a dict, receives the plan's facts
+    (the rows per block of a contiguous axis in row blocks: the oracle must
+    restart its decomposition at the same sources)."""
     H = _hjlo()
     plan = H.Plan(shape, dx, h, P, W, algo=H.ALGO_DECOMP)
-    assert plan.info()["algo"] == "decomp"
+    info = plan.info()
+    assert info["algo"] == "decomp"
+    if facts is not None:
+        facts.update(info)
     if eta:
         plan.set_tolerance(eta)
     u = torch.tensor(u0, device="cuda")
@@ -54,8 +60,9 @@ def test_bitwise_vs_oracle_method(case, eta):
     u0 = np.cumsum(rng.normal(size=shape), axis=-1) * 0.03
     V = rng.normal(size=shape) * 0.2
     n = 3
-    ref, ncomp = O.decomp_run(u0, dx, h, P, W, V, n, eta)
-    got, cnt = gpu_decomp(shape, dx, h, P, W, u0, V, n, eta)
+    facts = {}
+    got, cnt = gpu_decomp(shape, dx, h, P, W, u0, V, n, eta, facts=facts)
+    ref, ncomp = O.decomp_run(u0, dx, h, P, W, V, n, eta, block_rows=facts["block_rows"][-1])
     assert cnt["error_flags"] == 0
     assert np.array_equal(got.view(np.int64), ref.view(np.int64))
     assert cnt["components"] == ncomp
@@ -82,12 +89,13 @@ def test_graph_path_and_tolerance_change():
     u0 = np.cumsum(rng.normal(size=shape)) * 0.02
     V = rng.normal(size=shape) * 0.1
     plan = H.Plan(shape, dx, h, P, W, algo=H.ALGO_DECOMP)
+    R = plan.info()["block_rows"][0]
     Vt = torch.tensor(V, device="cuda")
     for eta in (0.0, 5e-3, 0.0):
         plan.set_tolerance(eta)
         u = torch.tensor(u0, device="cuda")
         plan.run(u, Vt, 40)
-        ref, _ = O.decomp_run(u0, dx, h, P, W, V, 40, eta)
+        ref, _ = O.decomp_run(u0, dx, h, P, W, V, 40, eta, block_rows=R)
         assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64)), eta
     plan.close()
 
@@ -116,3 +124,24 @@ def test_unsupported_uses_are_errors():
     with pytest.raises(H.HjloError):
         mono.set_tolerance(0.1)
     mono.close()
+
+
+@pytest.mark.parametrize("eta", [0.0, 1.0, 10.0])
+def test_row_blocks(eta):
+    """A single long line in row blocks: each block is decomposed on its own
+    span.  Bit for bit against the oracle's method restarted at the same
+    blocks, the same number of components, and at eta = 0 equal to the
+    scheme itself."""
+    N, W, h, P, n = 12000, 40, 2e-3, 0.3, 4
+    x = np.arange(N) / N
+    rng = np.random.default_rng(13)
+    u0 = 0.3 * np.sin(6 * np.pi * x) + 0.01 * np.cumsum(rng.normal(size=N)) / np.sqrt(N)
+    V = 0.2 * np.cos(4 * np.pi * x)
+    facts = {}
+    got, cnt = gpu_decomp((N,), 1.0 / N, h, P, W, u0, V, n, eta, facts=facts)
+    assert facts["row_blocks"][0] > 1 and cnt["error_flags"] == 0
+    ref, ncomp = O.decomp_run(u0, 1.0 / N, h, P, W, V, n, eta, block_rows=facts["block_rows"][0])
+    assert np.array_equal(got.view(np.int64), ref.view(np.int64))
+    assert cnt["components"] == ncomp
+    if eta == 0.0:
+        assert np.array_equal(got.view(np.int64), O.run(u0, 1.0 / N, h, P, W, V, n).view(np.int64))
