@@ -30,6 +30,12 @@ namespace {
 
 constexpr int kDecompThreads = 1024;   // upper bound; shape_decomp picks 256 or 1024
 constexpr unsigned kConvexBit = 0x80000000u;
+constexpr unsigned kLongBit = 0x40000000u;     // listed for the whole CTA (see below)
+constexpr unsigned kIndexMask = 0x3fffffffu;
+constexpr int kLongComponent = 512;    // components of at least this many pieces: the whole CTA
+constexpr int kMaxLong = 64;           // listed long components per CTA (the rest stay with a warp)
+constexpr int kMiscWarpTotals = 4;     // misc[4..36): warp totals of a block scan
+constexpr int kMiscLongList = 36;      // misc[36..36+kMaxLong): indices of the long components
 
 struct DecompParams {
     const double *src;
@@ -155,6 +161,68 @@ __device__ void conv_component_warp(const double *f, const double *r, int n, con
     __syncwarp();
 }
 
+// The same convolution as conv_component_warp by the whole CTA (every thread
+// calls it): the pieces' searches and the emissions are spread over all
+// threads and the running maximum of F is a block-wide scan (warp scans,
+// then a scan of the warps' totals in wtot[0..32)).  For the long components
+// that tolerance eta > 0 leaves, which would keep one warp busy while the
+// others wait at the barrier.
+__device__ void conv_component_block(const double *f, const double *r, int n, const double *g, int m, int s,
+                                     bool convex, int *F, unsigned long long *keys, int N, int *wtot)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    for (int j = tid; j < m; j += nthr) F[j] = below(r, n, __dsub_rn(g[j + 1], g[j]));
+    __syncthreads();
+    if (convex || m == 0) {
+        int carry = 0;
+        for (int j0 = 0; j0 < m; j0 += nthr) {
+            const int j = j0 + tid;
+            int v = (j < m) ? F[j] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int w = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = max(v, w);
+            }
+            if (lane == 31) wtot[warp] = v;
+            __syncthreads();
+            if (warp == 0) {
+                int t = (lane < nw) ? wtot[lane] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int w = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t = max(t, w);
+                }
+                if (lane < nw) wtot[lane] = t;
+            }
+            __syncthreads();
+            v = max(v, carry);
+            if (warp > 0) v = max(v, wtot[warp - 1]);
+            if (j < m) F[j] = v;
+            const int next = max(carry, wtot[nw - 1]);
+            __syncthreads();                         // wtot is rewritten by the next chunk
+            carry = next;
+        }
+        __syncthreads();
+        if (tid == 0) emit(keys, n, N, s, __dadd_rn(f[0], g[0]));
+        for (int j = tid; j < m; j += nthr) {
+            const int i = F[j];
+            emit(keys, n, N, s + i + j + 1, __dadd_rn(f[i], g[j + 1]));
+        }
+        for (int i = tid; i < n; i += nthr) {
+            const int J = upto(F, m, i);
+            emit(keys, n, N, s + i + 1 + J, __dadd_rn(f[i + 1], g[J]));
+        }
+    } else {
+        const int a0 = F[0], am = F[m - 1];
+        for (int x = tid; x <= a0; x += nthr) emit(keys, n, N, s + x, __dadd_rn(f[x], g[0]));
+        for (int j = tid; j < m; j += nthr) {
+            const int a = F[j];
+            emit(keys, n, N, s + j + a, __dadd_rn(f[a], g[j]));
+            emit(keys, n, N, s + j + 1 + a, __dadd_rn(f[a], g[j + 1]));
+        }
+        for (int x = m + am + tid; x <= m + n; x += nthr) emit(keys, n, N, s + x, __dadd_rn(f[x - m], g[m]));
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -221,9 +289,11 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     __syncthreads();
 
     // ---- greedy cut: a component starting at s takes the kind of the
-    // increment at s + 1 and ends at the first later point that breaks it
+    // increment at s + 1 and ends at the first later point that breaks it;
+    // components of kLongComponent pieces or more (up to kMaxLong of them)
+    // are flagged and listed for the whole CTA
     if (tid == 0) {
-        int nc = 0;
+        int nc = 0, nl = 0;
         if (L == 1) {
             comp[nc++] = 0u | kConvexBit;
             comp[nc] = 0u;
@@ -236,22 +306,35 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
                     convex = (cv[(s + 1) >> 5] >> ((s + 1) & 31)) & 1u;
                     e = next_clear(convex ? cv : cc, s + 2, L - 2, L - 1);
                 }
-                comp[nc++] = (unsigned)s | (convex ? kConvexBit : 0u);
+                const bool is_long = (e - s >= kLongComponent) && nl < kMaxLong;
+                if (is_long) misc[kMiscLongList + nl++] = nc;
+                comp[nc++] = (unsigned)s | (convex ? kConvexBit : 0u) | (is_long ? kLongBit : 0u);
                 s = e;
             }
             comp[nc] = (unsigned)(L - 1);
         }
         misc[0] = nc;
+        misc[1] = nl;
         atomicAdd(&p.counters[CNT_COMPONENTS], (unsigned long long)nc);
     }
     __syncthreads();
 
-    // ---- convolve the components (a warp each), minimum into the keys
-    const int nc = misc[0];
+    // ---- convolve the components, minimum into the keys: long ones by the
+    // whole CTA one after another, the others a warp each (the keys' minimum
+    // does not depend on the order)
+    const int nc = misc[0], nl = misc[1];
+    for (int q = 0; q < nl; ++q) {
+        const int c = misc[kMiscLongList + q];
+        const int s = (int)(comp[c] & kIndexMask);
+        const int e = (int)(comp[c + 1] & kIndexMask);
+        conv_component_block(f, r, n, g + s, e - s, s, (comp[c] & kConvexBit) != 0, fm + s, keys, N,
+                             misc + kMiscWarpTotals);
+    }
     for (int c = tid >> 5; c < nc; c += nthr >> 5) {
-        const int s = (int)(comp[c] & ~kConvexBit);
+        if (comp[c] & kLongBit) continue;
+        const int s = (int)(comp[c] & kIndexMask);
         const bool convex = (comp[c] & kConvexBit) != 0;
-        const int e = (int)(comp[c + 1] & ~kConvexBit);
+        const int e = (int)(comp[c + 1] & kIndexMask);
         conv_component_warp(f, r, n, g + s, e - s, s, convex, fm + s, keys, N);
     }
     __syncthreads();
@@ -292,7 +375,7 @@ size_t decomp_smem(const AxisPlan &ax, long long N, DecompParams *p)
     const size_t off_fm = off;
     off += sizeof(int) * (L + 1);
     const size_t off_misc = off;
-    off += 16;
+    off += sizeof(int) * (kMiscLongList + kMaxLong);            // counts, warp totals, long list
     if (p) {
         p->off_f = (int)off_f;
         p->off_r = (int)off_r;

@@ -145,3 +145,22 @@ def test_row_blocks(eta):
     assert cnt["components"] == ncomp
     if eta == 0.0:
         assert np.array_equal(got.view(np.int64), O.run(u0, 1.0 / N, h, P, W, V, n).view(np.int64))
+
+
+@pytest.mark.parametrize("eta", [0.0, 1.0])
+def test_long_components_by_the_whole_block(eta):
+    """Smooth lines of 1200 points decompose into components of 500 to 1260
+    pieces (convolved by the whole CTA) next to short ones (a warp each):
+    bit for bit against the oracle's method, the same component count."""
+    shape = (80, 1200)
+    x = np.arange(shape[0])[:, None] / shape[0]
+    y = np.arange(shape[1])[None, :] / shape[1]
+    u0 = np.cos(2 * np.pi * y) + 0.1 * np.cos(2 * np.pi * x)
+    V = 0.1 * np.cos(2 * np.pi * x) + 0.05 * np.cos(2 * np.pi * y)
+    dx, h, P, W, n = (1 / 80, 1 / 1200), 0.01, (0.2, 0.3), (4, 30), 3
+    facts = {}
+    got, cnt = gpu_decomp(shape, dx, h, P, W, u0, V, n, eta, facts=facts)
+    assert facts["row_blocks"] == [1, 1] and cnt["error_flags"] == 0
+    ref, ncomp = O.decomp_run(u0, dx, h, P, W, V, n, eta)
+    assert np.array_equal(got.view(np.int64), ref.view(np.int64))
+    assert cnt["components"] == ncomp
