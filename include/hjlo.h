@@ -186,14 +186,16 @@ hjlo_status hjlo_plan_set_tolerance(hjlo_plan *plan, double eta);
  * Autotune the launch shapes of a plan's monotone passes (no counterpart in
  * the paper: results never depend on the launch shape, only the time does).
  * Axis by axis, shapes around the current one -- lanes per line and lines
- * per tile halved / kept / doubled, wide-bracket offload on / off -- are
+ * per tile halved / kept / doubled, wide-bracket offload on / off, and for
+ * an axis in row blocks the rows per block halved / kept / doubled -- are
  * timed with CUDA events on nsteps steps from a device copy of u (u itself
  * is not modified; V: npts binary64 or NULL), and each axis keeps the
- * fastest (a candidate must beat the incumbent by 2 %).  Synchronous; the
- * plan's cached graph is rebuilt on next use.  report (host, may be NULL)
- * receives the choice.  Brute-force and decomposition axes are left as they
- * are.  Errors: HJLO_EINVAL (NULL plan/u, nsteps < 1), HJLO_ENOMEM,
- * HJLO_ECUDA.
+ * fastest (a candidate must beat the incumbent by 2 %).  Trial launches
+ * leave the plan's counters as they were.  Synchronous; the plan's cached
+ * graph is rebuilt on next use.  report (host, may be NULL) receives the
+ * choice (hjlo_plan_info gives the row blocks).  Brute-force and
+ * decomposition axes are left as they are.  Errors: HJLO_EINVAL (NULL
+ * plan/u, nsteps < 1), HJLO_ENOMEM, HJLO_ECUDA.
  */
 hjlo_status hjlo_plan_autotune(hjlo_plan *plan, const void *u, const double *V, int64_t nsteps,
                                hjlo_tune_report *report);
