@@ -90,13 +90,19 @@ __device__ int next_clear(const unsigned *bits, int from, int to, int none)
     }
 }
 
-// Number of kernel slopes r[0..n) strictly below rho (r increasing).
-__device__ __forceinline__ int below(const double *r, int n, double rho)
+// Number of kernel slopes strictly below rho (the slopes increase).  The
+// slopes are held as order-preserving keys (kh, kl: dkey32's words, which
+// compare as the finite values do, -0 with +0), so the search uses 32-bit
+// integer compares and leaves the binary64 pipe to the candidates' adds.
+__device__ __forceinline__ int below(const unsigned *kh, const unsigned *kl, int n, double rho)
 {
+    unsigned h, l;
+    dkey32(rho, h, l);
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (r[mid] < rho) lo = mid + 1; else hi = mid;
+        const unsigned a = kh[mid];
+        if (a < h || (a == h && kl[mid] < l)) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
@@ -120,11 +126,11 @@ __device__ __forceinline__ int upto(const int *F, int m, int i)
 // (Fmax(j), j + 1); kernel piece i is taken after J(i) = #{j : Fmax(j) <= i}
 // component pieces, giving the vertex (i + 1, J(i)).  Concave kind: alpha_j =
 // F(j) and the three parts of Theorem th:ccc.
-__device__ void conv_component_warp(const double *f, const double *r, int n, const double *g, int m, int s,
+__device__ void conv_component_warp(const double *f, const unsigned *rk, int n, const double *g, int m, int s,
                                     bool convex, int *F, unsigned long long *keys, int N)
 {
     const int lane = threadIdx.x & 31;
-    for (int j = lane; j < m; j += 32) F[j] = below(r, n, __dsub_rn(g[j + 1], g[j]));
+    for (int j = lane; j < m; j += 32) F[j] = below(rk, rk + n, n, __dsub_rn(g[j + 1], g[j]));
     __syncwarp();
     if (convex || m == 0) {
         int carry = 0;
@@ -167,11 +173,11 @@ __device__ void conv_component_warp(const double *f, const double *r, int n, con
 // then a scan of the warps' totals in wtot[0..32)).  For the long components
 // that tolerance eta > 0 leaves, which would keep one warp busy while the
 // others wait at the barrier.
-__device__ void conv_component_block(const double *f, const double *r, int n, const double *g, int m, int s,
+__device__ void conv_component_block(const double *f, const unsigned *rk, int n, const double *g, int m, int s,
                                      bool convex, int *F, unsigned long long *keys, int N, int *wtot)
 {
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-    for (int j = tid; j < m; j += nthr) F[j] = below(r, n, __dsub_rn(g[j + 1], g[j]));
+    for (int j = tid; j < m; j += nthr) F[j] = below(rk, rk + n, n, __dsub_rn(g[j + 1], g[j]));
     __syncthreads();
     if (convex || m == 0) {
         int carry = 0;
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     double *g = reinterpret_cast<double *>(smem);
     double *f = reinterpret_cast<double *>(smem + p.off_f);
-    double *r = reinterpret_cast<double *>(smem + p.off_r);
+    unsigned *rk = reinterpret_cast<unsigned *>(smem + p.off_r);   // slope keys: high words, then low
     int *fm = reinterpret_cast<int *>(smem + p.off_fm);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem + p.off_keys);
     unsigned *cv = reinterpret_cast<unsigned *>(smem + p.off_cv);
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
     for (int i = tid; i <= n; i += nthr) f[i] = p.kr64[n - i];
     for (int x = tid; x < N; x += nthr) keys[x] = ~0ull;
     __syncthreads();
-    for (int i = tid; i < n; i += nthr) r[i] = __dsub_rn(f[i + 1], f[i]);      // kernel slopes
+    for (int i = tid; i < n; i += nthr) dkey32(__dsub_rn(f[i + 1], f[i]), rk[i], rk[n + i]);   // kernel slopes
 
     // ---- kinds of the slope increment at every interior point q:
     // convex rule (increment >= -eta) and concave rule (increment <= 0)
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
         const int c = misc[kMiscLongList + q];
         const int s = (int)(comp[c] & kIndexMask);
         const int e = (int)(comp[c + 1] & kIndexMask);
-        conv_component_block(f, r, n, g + s, e - s, s, (comp[c] & kConvexBit) != 0, fm + s, keys, N,
+        conv_component_block(f, rk, n, g + s, e - s, s, (comp[c] & kConvexBit) != 0, fm + s, keys, N,
                              misc + kMiscWarpTotals);
     }
     for (int c = tid >> 5; c < nc; c += nthr >> 5) {
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(kDecompThreads) decomp_kernel(DecompParams p)
         const int s = (int)(comp[c] & kIndexMask);
         const bool convex = (comp[c] & kConvexBit) != 0;
         const int e = (int)(comp[c + 1] & kIndexMask);
-        conv_component_warp(f, r, n, g + s, e - s, s, convex, fm + s, keys, N);
+        conv_component_warp(f, rk, n, g + s, e - s, s, convex, fm + s, keys, N);
     }
     __syncthreads();
 
@@ -361,7 +367,7 @@ size_t decomp_smem(const AxisPlan &ax, long long N, DecompParams *p)
     off += sizeof(double) * L;                                  // g
     const size_t off_f = off;
     off += sizeof(double) * (n + 1);
-    const size_t off_r = off;
+    const size_t off_r = off;                                   // n slope keys (two words each)
     off += sizeof(double) * (n + 1);
     off = (off + 15) & ~size_t(15);
     const size_t off_keys = off;

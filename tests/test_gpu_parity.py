@@ -303,3 +303,35 @@ def test_segment_shapes_with_shocks(lanes, offload, monkeypatch):
     got, am, _ = gpu_run(shape, dx, h, P, W, u0, V, 2, algo=2, argmin=True)
     assert np.array_equal(got.view(np.int64), ref.view(np.int64))
     assert np.array_equal(am, ref_am)
+
+
+def test_resume_equals_uninterrupted_run():
+    """Checkpoint and resume (the semigroup property of eq. uN): n steps, a
+    copy of the state, then m more steps equal n + m steps bit for bit -- for
+    a static V through the captured 16-step graphs and single steps, and for a
+    time-dependent V whose rows continue where the first run stopped."""
+    shape, dx, h, P, W = (40, 56), (1 / 40, 1 / 56), 0.05, (0.3, -0.2), (5, 7)
+    u0, V = gen(shape, 21)
+    H = _hjlo()
+    plan = H.Plan(shape, dx, h, P, W)
+    Vt = torch.tensor(V, device="cuda")
+    whole = torch.tensor(u0, device="cuda")
+    plan.run(whole, Vt, 37)
+    part = torch.tensor(u0, device="cuda")
+    plan.run(part, Vt, 20)
+    resumed = part.clone()                       # the checkpoint
+    plan.run(resumed, Vt, 17)
+    assert torch.equal(whole, resumed)
+    assert np.array_equal(whole.cpu().numpy().view(np.int64), O.run(u0, dx, h, P, W, V, 37).view(np.int64))
+    Vs = np.random.default_rng(22).normal(size=(30, *shape)) * 0.2
+    Vst = torch.tensor(Vs, device="cuda")
+    a = torch.tensor(u0, device="cuda")
+    plan.run_tv(a, Vst, 30)
+    b = torch.tensor(u0, device="cuda")
+    plan.run_tv(b, Vst[:11].contiguous(), 11)
+    plan.run_tv(b, Vst[11:].contiguous(), 19)
+    assert torch.equal(a, b)
+    assert np.array_equal(a.cpu().numpy().view(np.int64),
+                          O.run(u0, dx, h, P, W, Vs, 30, V_per_step=True).view(np.int64))
+    assert plan.sync()["steps"] == 37 + 20 + 17 + 30 + 11 + 19
+    plan.close()
