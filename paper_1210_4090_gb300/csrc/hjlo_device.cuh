@@ -82,11 +82,14 @@ struct PassParams {
     int wide_mul, wide_add;   // MONGE: a bracket of more than wide_mul * (expected span) + wide_add
                               // offsets is searched by the whole warp
     int edge;                 // partial window: count argmins on its first or last displacement
+    int rows;                 // rows searched per line: N, or in row-block mode the block's vR
     // Row blocks (contiguous lines only; vN = 0 otherwise).  A line of vN points
     // is cut into vblocks blocks of vR rows; block b of real line rl is the
     // tile line rl * vblocks + b, staged as a periodic line of N = vR + weff - 1
     // points: halo index jj <-> real position (b * vR + jj + vhoff) mod vN.
-    // Its first vR rows see no wrap, so their minima are the real rows'.
+    // Its first vR rows see no wrap, so their minima are the real rows', and
+    // only they are searched: the last segment's right bracket is row N,
+    // the periodic image of row 0, a valid bracket for every row of the line.
     long long vN, vblocks;
     int vR, vhoff;
 };
@@ -766,9 +769,10 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         const bool work = active && !fallback;
         int rescans = 0;
         const int S = p.seg, GS = p.gs;
-        const int s0 = min(g * S, N), s1 = min((g + 1) * S, N);
+        const int NR = p.rows;                // rows searched (N, or a row block's vR)
+        const int s0 = min(g * S, NR), s1 = min((g + 1) * S, NR);
         const int o = g & (GS - 1);
-        const int rp = min((g - o) * S, N);   // the group's pivot row
+        const int rp = min((g - o) * S, NR);  // the group's pivot row
         if (active && fallback) {
             // brute force over each lane's own segment of rows
             for (int r = s0; r < s1; ++r) {
@@ -790,7 +794,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             // group's first row; partial minima merge by shuffles
             const int ch = (weff + GS - 1) / GS;
             const int tlo = o * ch, thi = min(tlo + ch, weff) - 1;
-            const bool hp = work && rp < N;
+            const bool hp = work && rp < NR;
             int m1 = 0x7fffffff, m2 = 0x7fffffff, t1 = 0x7fffffff;
             if (hp) {
                 const int *f = lfx + rp;
@@ -844,8 +848,8 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 int lo = 0, hi = 0;
                 if (has) {
                     const int jl = rp + lt[rp];
-                    const int rn = min((g - o + GS) * S, N);
-                    const int jr = (rn < N) ? rn + lt[rn] : N + lt[0];
+                    const int rn = min((g - o + GS) * S, NR);
+                    const int jr = (rn < NR) ? rn + lt[rn] : N + lt[0];
                     lo = max(jl - s0, 0);
                     hi = min(jr - s0, weff - 1);
                     if (lo > hi) { lo = 0; hi = weff - 1; }   // never for a Monge matrix
@@ -863,7 +867,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
             // every lane walks the block-uniform segment length S (rows past
             // its segment's end are predicated off)
             const bool dc = work && s1 - s0 >= 2;
-            const int jnext = dc ? ((s1 < N) ? (s1 + lt[s1]) : (N + lt[0])) : 0;
+            const int jnext = dc ? ((s1 < NR) ? (s1 + lt[s1]) : (N + lt[0])) : 0;
             const int nr = s1 - s0;
             int step = 1;
             while (step * 2 < S) step *= 2;
@@ -903,8 +907,8 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 int l = cl, r0 = 0, r1 = N;
                 if (lpl >= 32) {
                     const int w0 = (g >> 5) << 5;                    // first lane of the warp in the line
-                    r0 = min(w0 * S, N);
-                    r1 = min((w0 + 32) * S, N);
+                    r0 = min(w0 * S, NR);
+                    r1 = min((w0 + 32) * S, NR);
                 } else {
                     l = ((warp << 5) >> p.log2lpl) + k;
                 }
@@ -926,7 +930,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         if (line < tl.valid) {
             unsigned short *lt = tt + line * p.tp;
             const int wl = warp - line * p.wpl;
-            for (int r = wl; r < N; r += p.wpl) {
+            for (int r = wl; r < p.rows; r += p.wpl) {
                 // running minimum as a Key2: the binary64 pipe only does the adds
                 Key2 best = key2_max();
                 int bt = 0;

@@ -35,6 +35,7 @@ struct AxisPlan {
     // points (see PassParams); the launch fields below then describe those
     long long vblocks = 1, vNp = 0;
     int vR = 0;
+    long long rows = 0;                    // rows searched per launched line (0: all N)
     int by = 1, nbox = 1, lp = 0;
     long long ntiles = 0, tiles_per_outer = 1;
     size_t smem = 0;

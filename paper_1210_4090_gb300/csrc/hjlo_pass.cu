@@ -272,6 +272,7 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
     ax.vblocks = 1;
     ax.vR = 0;
     ax.vNp = 0;
+    ax.rows = 0;
     if ((algo == KALGO_MONGE || algo == KALGO_BRUTE) && row_blocks) {
         const ShapeHints hint = hints ? *hints : env_hints();
         const long long vR = block_rows(ax, esize, algo, num_sms, smem_optin, hint.block_rows);
@@ -281,6 +282,7 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
             v.vblocks = (ax.N + vR - 1) / vR;
             v.outer = ax.outer * v.vblocks;
             v.hoff = 0;
+            v.rows = vR;                      // only the block's own rows are searched
             hjlo_status s = shape_lines(v, esize, algo, num_sms, smem_optin, 1, hints);
             if (s != HJLO_OK) return s;
             // launch fields from the block lines; geometry and tables stay the axis's
@@ -290,6 +292,7 @@ hjlo_status shape_launch(AxisPlan &ax, int esize, int algo, int num_sms, size_t 
             r.hoff = ax.hoff;
             r.vR = (int)vR;
             r.vNp = v.N;
+            r.rows = 0;
             ax = r;
             return HJLO_OK;
         }
@@ -324,6 +327,8 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
         cmax = (int)std::max<long long>(p2, cmin);
     }
 
+    // rows searched per line (a row block searches only its own rows)
+    const long long NR = (ax.rows > 0 && ax.rows < N) ? ax.rows : N;
     if (algo == KALGO_MONGE) {
         // lanes per line: maximise (occupancy efficiency) / (work per row), with
         // work per row ~ weff/S + log2(S) + 3 (pivot share, divide and conquer,
@@ -332,7 +337,7 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
         int best_lpl = 1;
         double best_score = -1.0;
         for (int lpl = 1; lpl <= 1024; lpl *= 2) {
-            int S = odd_at_least((N + lpl - 1) / lpl);
+            int S = odd_at_least((NR + lpl - 1) / lpl);
             AxisPlan t = ax;
             t.lpl = lpl;
             t.seg = S;
@@ -354,7 +359,7 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
         if (best_lpl > N) best_lpl = 1;
         ax.lpl = best_lpl;
         ax.log2lpl = ilog2(best_lpl);
-        ax.seg = odd_at_least((N + best_lpl - 1) / best_lpl);
+        ax.seg = odd_at_least((NR + best_lpl - 1) / best_lpl);
         ax.gs = pivot_group(ax.weff, ax.seg, ax.lpl, nullptr);
         // offload rule of wide brackets: 2 x expected span + 8 unless hinted
         ax.wide_mul = 2;
@@ -538,6 +543,7 @@ static void fill_params(const AxisPlan &ax, PassParams &p)
     p.wide_mul = ax.wide_mul;
     p.wide_add = ax.wide_add;
     p.edge = (ax.weff < ax.N) ? 1 : 0;     // full torus windows have no edge
+    p.rows = (int)ax.N;
     if (ax.vblocks > 1) {
         p.N = ax.vNp;
         p.outer = ax.outer * ax.vblocks;
@@ -546,6 +552,7 @@ static void fill_params(const AxisPlan &ax, PassParams &p)
         p.vblocks = ax.vblocks;
         p.vR = ax.vR;
         p.vhoff = ax.hoff;
+        p.rows = ax.vR;
     }
 }
 
