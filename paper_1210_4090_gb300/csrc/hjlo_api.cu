@@ -97,16 +97,34 @@ hjlo_status set_device(const hjlo_plan *p)
     return HJLO_OK;
 }
 
-// All passes of one step.  src -> dst for axis 0, then in place on dst.
+bool ranges_overlap(const void *a, const void *b, size_t n)
+{
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
+}
+
+// All passes of one step.  src -> dst for axis 0, then in place on dst.  An
+// axis in row blocks cannot run in place: a block stages its rows' window
+// span, which holds rows of other blocks, and a block that starts late would
+// read rows another block has already written.  Such a pass writes to the
+// plan's scratch and is copied back (stream-ordered, so graphs capture it).
 hjlo_status enqueue_step(hjlo_plan *p, const void *src, void *dst, const double *hv, double hv_scale,
                          int32_t *amin, cudaStream_t st)
 {
+    const size_t bytes = (size_t)p->npts * p->esize;
     for (int a = 0; a < p->ndim; ++a) {
         const bool last = (a == p->ndim - 1);
-        hjlo_status s = launch_pass(p->ax[a], p->dtype, a == 0 ? src : dst, dst, last ? hv : nullptr,
+        const void *from = (a == 0) ? src : dst;
+        const bool via_scratch = p->ax[a].vblocks > 1 && ranges_overlap(from, dst, bytes);
+        if (via_scratch && !p->d_scratch) return set_error(HJLO_ECUDA, "row-block scratch missing");
+        hjlo_status s = launch_pass(p->ax[a], p->dtype, from, via_scratch ? p->d_scratch : dst, last ? hv : nullptr,
                                     last ? hv_scale : 0.0, amin ? amin + (long long)a * p->npts : nullptr,
                                     p->d_counters, p->d_flags, st);
         if (s != HJLO_OK) return s;
+        if (via_scratch) {
+            cudaError_t e = cudaMemcpyAsync(dst, p->d_scratch, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_error(e, "row-block copy");
+        }
     }
     return HJLO_OK;
 }
@@ -128,12 +146,6 @@ hjlo_status form_hv(hjlo_plan *p, const double *V)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "h*V kernel launch");
     return HJLO_OK;
-}
-
-bool ranges_overlap(const void *a, const void *b, size_t n)
-{
-    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
-    return x < y + n && y < x + n;
 }
 
 void destroy_graph(hjlo_plan *p)
@@ -280,6 +292,10 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
     }
     p->algo = (d->algo == HJLO_ALGO_DECOMP) ? HJLO_ALGO_DECOMP : (all_monge ? HJLO_ALGO_MONGE : HJLO_ALGO_BRUTE);
+    bool blocks = false;
+    for (int a = 0; a < p->ndim; ++a) blocks = blocks || p->ax[a].vblocks > 1;
+    s = blocks ? dmalloc(&p->d_scratch, (size_t)p->npts * p->esize, "cudaMalloc(row-block scratch)") : HJLO_OK;
+    if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
     s = dmalloc((void **)&p->d_counters, sizeof(unsigned long long) * CNT_N, "cudaMalloc(counters)");
     if (s == HJLO_OK) s = dmalloc((void **)&p->d_flags, sizeof(int), "cudaMalloc(flags)");
     if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
@@ -305,6 +321,7 @@ hjlo_status hjlo_plan_destroy(hjlo_plan *p)
     cudaFree(p->d_hv);
     cudaFree(p->d_part);
     cudaFree(p->d_u_host_run);
+    cudaFree(p->d_scratch);
     cudaFree(p->d_V_host_run);
     cudaFree(p->d_ckpt);
     cudaFree(p->d_amin);

@@ -163,6 +163,7 @@ struct hjlo_plan {
     double *d_hv = nullptr;                    // npts, h*V of the current run
     double *d_part = nullptr;                  // readout partials
     void *d_u_host_run = nullptr;              // hjlo_run_host staging
+    void *d_scratch = nullptr;                 // npts values: output of in-place row-block passes
     double *d_V_host_run = nullptr;
     hjlo::GraphCache graph;
     long long steps = 0;

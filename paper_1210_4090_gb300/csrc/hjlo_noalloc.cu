@@ -178,7 +178,9 @@ extern "C" hjlo_status hjlo_step_noalloc(const hjlo_desc *d, void *cuda_stream, 
         int algo = KALGO_MONGE;
         if (d->algo == HJLO_ALGO_BRUTE) algo = KALGO_BRUTE;
         if (d->algo == HJLO_ALGO_AUTO && (ax[a].weff < 8 || !(ax[a].curv > 0))) algo = KALGO_BRUTE;
-        if ((s = shape_launch(ax[a], esize, algo, df.num_sms, df.smem_optin)) != HJLO_OK) return s;
+        // whole lines only: row blocks cannot run in place and this step owns no scratch
+        if ((s = shape_launch(ax[a], esize, algo, df.num_sms, df.smem_optin, 1, nullptr, false)) != HJLO_OK)
+            return s;
         ax[a].d_kr64 = scr->kr64[a];
         // synchronous with respect to this host buffer for pageable memory
         cudaError_t e = cudaMemcpyAsync(ax[a].d_kr64, host_tab, sizeof(double) * ax[a].weff,

@@ -104,3 +104,25 @@ def test_whole_lines_when_they_fill_the_gpu():
     plan = hjlo.Plan((1024, 1024), (1 / 1024,) * 2, 0.02, (0.3, 0.1), (64, 64))
     assert plan.info()["row_blocks"] == [1, 1]
     plan.close()
+
+
+def test_row_blocks_in_place_over_two_waves():
+    """40 lines of 60000 points: 4 row blocks per line of ~15800 rows, 160
+    CTAs of 1024 threads with ~220 KB of shared memory each -- more than one
+    per SM, so some start after others have finished.  A block stages rows of
+    its neighbours, so a pass in place (hjlo_run) must not write over rows a
+    later block has yet to read: the plan routes it through its scratch."""
+    shape, h, P, W, n = (40, 60000), 1e-4, (0.1, 0.2), (1, 30), 2
+    dx = tuple(1.0 / s for s in shape)
+    u0, V = _data(shape, False, 10)
+    from paper_1210_4090_gb300 import hjlo
+    plan = hjlo.Plan(shape, dx, h, P, W)
+    info = plan.info()
+    assert info["row_blocks"][1] > 1, info
+    u = torch.tensor(u0, device="cuda")
+    plan.run(u, torch.tensor(V, device="cuda"), n)
+    assert plan.sync()["error_flags"] == 0
+    plan.close()
+    ref = O.run(u0, dx, h, P, W, V, n)
+    bad = np.flatnonzero(u.cpu().numpy().view(np.int64) != ref.view(np.int64))
+    assert bad.size == 0, "%d mismatches, first at %d" % (bad.size, bad[0])

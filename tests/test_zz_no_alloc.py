@@ -17,7 +17,7 @@ CASES = [
     # shape, dx, h, P, W
     ((48, 72), (1 / 48, 1 / 72), 0.05, (0.3, -0.2), (6, 9)),
     ((12, 20, 24), (1 / 12, 1 / 20, 1 / 24), 0.08, (0.2, -0.1, 0.35), (3, 4, 0)),
-    ((400,), 1 / 400, 0.05, 0.3, 20),                 # one line: launched in row blocks
+    ((400,), 1 / 400, 0.05, 0.3, 20),                 # one line: the plan runs it in row blocks, this step whole
 ]
 
 
