@@ -382,6 +382,32 @@ hjlo_status hjlo_integral_destroy(hjlo_integral *plan);
 hjlo_status hjlo_step_noalloc(const hjlo_desc *desc, void *cuda_stream, const void *u_in, void *u_out,
                               const double *V);
 
+/* Launch shape of one axis pass (host struct; see hjlo_shape_query). */
+typedef struct {
+    int32_t lanes_per_line;       /* threads per launched line (monotone search: lanes, one segment each) */
+    int32_t segment_rows;         /* monotone search: rows per lane segment (odd); brute force: 1 */
+    int32_t lines_per_tile;       /* launched lines per CTA */
+    int32_t threads;              /* threads per CTA */
+    int64_t smem_bytes;           /* dynamic shared memory per CTA */
+    int64_t tiles;                /* CTAs per pass launch */
+    int64_t row_blocks;           /* 1: whole lines; k > 1: every line cut into k blocks of rows */
+    int64_t block_rows;           /* rows per block (the last holds the rest); 0 for whole lines */
+    int64_t line_points;          /* points staged per launched line: N, or block_rows + weff - 1 */
+} hjlo_shape_info;
+
+/*
+ * The launch shape that hjlo_plan_create chooses for a contiguous axis of
+ * `lines` lines of N points with a window of weff displacements (1 <= weff
+ * <= N; weff = N is the full torus window), for a GPU with num_sms SMs and
+ * smem_optin bytes of opt-in shared memory per CTA.  Host only: no device is
+ * touched.  esize: 8 (binary64) or 4 (binary32 storage); algo:
+ * HJLO_ALGO_BRUTE or HJLO_ALGO_MONGE.  The environment's tuning overrides
+ * apply as for a plan.  Errors: HJLO_EINVAL (bad arguments, NULL out),
+ * HJLO_EUNSUPPORTED (the lines do not fit and cannot run in row blocks).
+ */
+hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esize, int32_t algo, int32_t num_sms,
+                             int64_t smem_optin, hjlo_shape_info *out);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char *hjlo_last_error(void);
 

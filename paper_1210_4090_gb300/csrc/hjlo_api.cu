@@ -221,6 +221,37 @@ extern "C" {
 
 int32_t hjlo_version(void) { return HJLO_VERSION; }
 
+hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esize, int32_t algo, int32_t num_sms,
+                             int64_t smem_optin, hjlo_shape_info *out)
+{
+    clear_error();
+    if (!out || N < 1 || N > (1LL << 30) || lines < 1 || weff < 1 || weff > N ||
+        (esize != 8 && esize != 4) || (algo != HJLO_ALGO_BRUTE && algo != HJLO_ALGO_MONGE) || num_sms < 1 ||
+        smem_optin < 1024)
+        return set_error(HJLO_EINVAL, "invalid shape query");
+    if (weff > 65535) return set_error(HJLO_EUNSUPPORTED, "window of %lld displacements exceeds 65535", (long long)weff);
+    AxisPlan ax;
+    ax.N = N;
+    ax.inner = 1;
+    ax.outer = lines;
+    ax.weff = (int)weff;
+    ax.hoff = 0;
+    hjlo_status s = shape_launch(ax, esize, algo == HJLO_ALGO_BRUTE ? KALGO_BRUTE : KALGO_MONGE, num_sms,
+                                 (size_t)smem_optin);
+    if (s != HJLO_OK) return s;
+    memset(out, 0, sizeof(*out));
+    out->lanes_per_line = ax.lpl;
+    out->segment_rows = ax.seg;
+    out->lines_per_tile = ax.C;
+    out->threads = ax.threads;
+    out->smem_bytes = (int64_t)ax.smem;
+    out->tiles = ax.ntiles;
+    out->row_blocks = ax.vblocks;
+    out->block_rows = (ax.vblocks > 1) ? ax.vR : 0;
+    out->line_points = (ax.vblocks > 1) ? ax.vNp : N;
+    return HJLO_OK;
+}
+
 const char *hjlo_last_error(void) { return last_error_cstr(); }
 
 hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **out)

@@ -399,7 +399,7 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
     layout_smem(ax, esize, algo);
     if (ax.smem > smem_optin || (long long)C * lanes > 1024)
         return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit in shared memory", N);
-    const size_t budget = 110 * 1024;
+    const size_t budget = std::min<size_t>(110 * 1024, smem_optin);
     const long long cap = (algo == KALGO_MONGE) ? 128 : 512;
     while (2 * C <= std::max(cmax, C) && (long long)2 * C * lanes <= cap &&
            tiles_for(2 * C) * std::max(1LL, replicas) >= 2LL * num_sms) {

@@ -68,8 +68,15 @@ _lock = threading.Lock()
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/hjlo.h
+class ShapeInfo(ctypes.Structure):
+    _fields_ = [("lanes_per_line", _i32), ("segment_rows", _i32), ("lines_per_tile", _i32), ("threads", _i32),
+                ("smem_bytes", _i64), ("tiles", _i64), ("row_blocks", _i64), ("block_rows", _i64),
+                ("line_points", _i64)]
+
+
 _SIGS = [
     ("hjlo_version", _i32, []),
+    ("hjlo_shape_query", _i32, [_i64, _i64, _i64, _i32, _i32, _i32, _i64, ctypes.POINTER(ShapeInfo)]),
     ("hjlo_last_error", ctypes.c_char_p, []),
     ("hjlo_plan_create", _i32, [ctypes.POINTER(Desc), _vp, ctypes.POINTER(_vp)]),
     ("hjlo_plan_destroy", _i32, [_vp]),
@@ -107,6 +114,15 @@ def library_path() -> str:
 
 def exported_symbols() -> list[str]:
     return [s[0] for s in _SIGS]
+
+
+def shape_query(N, lines, weff, esize=8, algo=ALGO_MONGE, num_sms=152, smem_optin=232448) -> dict:
+    """The launch shape a plan would use for a contiguous axis (hjlo_shape_query;
+    host only, no device)."""
+    out = ShapeInfo()
+    _check(lib().hjlo_shape_query(int(N), int(lines), int(weff), int(esize), int(algo), int(num_sms),
+                                  int(smem_optin), ctypes.byref(out)), "hjlo_shape_query")
+    return {f: getattr(out, f) for f, _ in ShapeInfo._fields_}
 
 
 def lib() -> ctypes.CDLL:
