@@ -55,3 +55,47 @@ def test_random_geometry(i):
     if algo != 3:
         from edge_counts import edge_hits
         assert cnt["window_edge_hits"] == edge_hits(u0, dx, h, P, W, V, n)
+
+
+NDECOMP = 16
+
+
+def _decomp_case(i):
+    rng = np.random.default_rng([11, i])
+    ndim = int(rng.integers(1, 4))
+    cap = {1: 600, 2: 60, 3: 20}[ndim]
+    shape = tuple(int(rng.integers(1, cap)) for _ in range(ndim))
+    dx = tuple(1.0 / n for n in shape)
+    h = float(rng.uniform(0.02, 0.2))
+    P = tuple(float(rng.uniform(-2, 2)) for _ in range(ndim))
+    W = tuple(int(rng.choice([0, rng.integers(1, 6), rng.integers(4, 40)])) for _ in range(ndim))
+    u0 = np.cumsum(rng.normal(size=shape), axis=-1) * float(rng.choice([0.01, 0.05]))
+    V = rng.normal(size=shape) * 0.1 if rng.random() < 0.7 else None
+    n = int(rng.integers(1, 4))
+    eta = float(rng.choice([0.0, 0.0, 1.0, 10.0]))
+    return shape, dx, h, P, W, u0, V, n, eta
+
+
+@pytest.mark.parametrize("i", range(NDECOMP))
+def test_random_geometry_decomposition(i):
+    """The paper's Sec. 4 method on random geometries: bit for bit against the
+    oracle's version of the method (restarted at the plan's row blocks), the
+    same number of components."""
+    from paper_1210_4090_gb300 import hjlo
+    shape, dx, h, P, W, u0, V, n, eta = _decomp_case(i)
+    try:
+        plan = hjlo.Plan(shape, dx, h, P, W, algo=hjlo.ALGO_DECOMP)
+    except hjlo.HjloError as e:            # a non-strictly-convex table or a line too long
+        assert e.status in (4, 6), e
+        return
+    R = plan.info()["block_rows"][-1]
+    if eta:
+        plan.set_tolerance(eta)
+    u = torch.tensor(u0, device="cuda")
+    plan.run(u, None if V is None else torch.tensor(V, device="cuda"), n)
+    cnt = plan.sync()
+    plan.close()
+    ref, ncomp = O.decomp_run(u0, dx, h, P, W, V, n, eta, block_rows=R)
+    assert cnt["error_flags"] == 0
+    assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64)), (shape, W, P, eta)
+    assert cnt["components"] == ncomp
