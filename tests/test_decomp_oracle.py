@@ -137,3 +137,21 @@ def test_blocks_at_zero_tolerance_equal_the_scheme():
         assert np.array_equal(got.view(np.int64), ref.view(np.int64)), R
     whole, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, V, 3, 0.0)
     assert np.array_equal(whole.view(np.int64), ref.view(np.int64))
+
+
+@pytest.mark.parametrize("R", [24, 77, 300])
+def test_blocks_with_tolerance_stay_candidates(R):
+    """With eta > 0 and the decomposition restarted at each block of rows
+    (A27), every output is still one candidate of the scheme, so never below
+    the exact scheme's value, and the gap shrinks with eta."""
+    N, W, h = 300, 12, 0.01
+    x = np.arange(N) / N
+    rng = np.random.default_rng(6)
+    u0 = 0.3 * np.sin(6 * np.pi * x) + 0.01 * np.cumsum(rng.normal(size=N)) / np.sqrt(N)
+    exact = O.run(u0, 1.0 / N, h, 0.2, W, None, 1)
+    gaps = []
+    for eta in (0.5, 5.0, 50.0):
+        got, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, None, 1, eta, block_rows=R)
+        assert np.all(got >= exact), eta
+        gaps.append(float(np.max(got - exact)))
+    assert gaps[0] <= gaps[1] <= gaps[2], gaps
