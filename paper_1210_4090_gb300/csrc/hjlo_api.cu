@@ -129,6 +129,35 @@ hjlo_status enqueue_step(hjlo_plan *p, const void *src, void *dst, const double 
     return HJLO_OK;
 }
 
+// nsteps steps in place on u (V: nsteps rows, one per step, when tv; else
+// hv for every step).  Passes in row blocks alternate between u and the
+// plan's scratch instead of copying back after each one; the state is copied
+// to u at the end only when an odd number of them ran.
+hjlo_status enqueue_steps(hjlo_plan *p, void *u, const double *V, bool tv, long long nsteps, cudaStream_t st)
+{
+    void *cur = u;
+    for (long long n = 0; n < nsteps; ++n) {
+        const double *v = tv ? (V ? V + n * p->npts : nullptr) : V;
+        for (int a = 0; a < p->ndim; ++a) {
+            const bool last = (a == p->ndim - 1);
+            void *next = cur;
+            if (p->ax[a].vblocks > 1) {
+                if (!p->d_scratch) return set_error(HJLO_ECUDA, "row-block scratch missing");
+                next = (cur == u) ? p->d_scratch : u;
+            }
+            hjlo_status s = launch_pass(p->ax[a], p->dtype, cur, next, last ? v : nullptr,
+                                        (last && tv) ? p->desc.h : 0.0, nullptr, p->d_counters, p->d_flags, st);
+            if (s != HJLO_OK) return s;
+            cur = next;
+        }
+    }
+    if (cur != u) {
+        cudaError_t e = cudaMemcpyAsync(u, cur, (size_t)p->npts * p->esize, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_error(e, "row-block copy");
+    }
+    return HJLO_OK;
+}
+
 hjlo_status ensure_hv(hjlo_plan *p)
 {
     if (p->d_hv) return HJLO_OK;
@@ -160,8 +189,7 @@ hjlo_status capture_graph(hjlo_plan *p, void *u, const double *hv)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
-    hjlo_status s = HJLO_OK;
-    for (int k = 0; k < kGraphSteps && s == HJLO_OK; ++k) s = enqueue_step(p, u, u, hv, 0.0, nullptr, p->cap_stream);
+    hjlo_status s = enqueue_steps(p, u, hv, false, kGraphSteps, p->cap_stream);
     e = cudaStreamEndCapture(p->cap_stream, &g);
     if (s != HJLO_OK) { if (g) cudaGraphDestroy(g); return s; }
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
@@ -192,9 +220,9 @@ hjlo_status run_impl(hjlo_plan *p, void *u, const double *V, long long nsteps, b
             if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
         }
     }
-    for (; n < nsteps; ++n) {
-        const double *v = tv ? (V ? V + n * p->npts : nullptr) : hv;
-        hjlo_status s = enqueue_step(p, u, u, v, tv ? p->desc.h : 0.0, nullptr, p->stream);
+    if (n < nsteps) {
+        hjlo_status s = tv ? enqueue_steps(p, u, V ? V + n * p->npts : nullptr, true, nsteps - n, p->stream)
+                           : enqueue_steps(p, u, hv, false, nsteps - n, p->stream);
         if (s != HJLO_OK) return s;
     }
     p->steps += nsteps;
