@@ -401,8 +401,10 @@ typedef struct {
  * <= N; weff = N is the full torus window), for a GPU with num_sms SMs and
  * smem_optin bytes of opt-in shared memory per CTA.  Host only: no device is
  * touched.  esize: 8 (binary64) or 4 (binary32 storage); algo:
- * HJLO_ALGO_BRUTE or HJLO_ALGO_MONGE.  The environment's tuning overrides
- * apply as for a plan.  Errors: HJLO_EINVAL (bad arguments, NULL out),
+ * HJLO_ALGO_BRUTE, HJLO_ALGO_MONGE or HJLO_ALGO_DECOMP (binary64 only, a
+ * strictly convex table assumed; one CTA per line or row block, whose
+ * threads are reported as lanes_per_line, segment_rows 0).  The
+ * environment's tuning overrides apply as for a plan.  Errors: HJLO_EINVAL (bad arguments, NULL out),
  * HJLO_EUNSUPPORTED (the lines do not fit and cannot run in row blocks).
  */
 hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esize, int32_t algo, int32_t num_sms,

@@ -254,8 +254,9 @@ hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esi
 {
     clear_error();
     if (!out || N < 1 || N > (1LL << 30) || lines < 1 || weff < 1 || weff > N ||
-        (esize != 8 && esize != 4) || (algo != HJLO_ALGO_BRUTE && algo != HJLO_ALGO_MONGE) || num_sms < 1 ||
-        smem_optin < 1024)
+        (esize != 8 && esize != 4) ||
+        (algo != HJLO_ALGO_BRUTE && algo != HJLO_ALGO_MONGE && algo != HJLO_ALGO_DECOMP) ||
+        (algo == HJLO_ALGO_DECOMP && esize != 8) || num_sms < 1 || smem_optin < 1024)
         return set_error(HJLO_EINVAL, "invalid shape query");
     if (weff > 65535) return set_error(HJLO_EUNSUPPORTED, "window of %lld displacements exceeds 65535", (long long)weff);
     AxisPlan ax;
@@ -264,10 +265,26 @@ hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esi
     ax.outer = lines;
     ax.weff = (int)weff;
     ax.hoff = 0;
+    ax.curv = 1.0;                               // a strictly convex table (the decomposition pass needs one)
+    memset(out, 0, sizeof(*out));
+    if (algo == HJLO_ALGO_DECOMP) {
+        hjlo_status s = shape_decomp(ax, (size_t)smem_optin, num_sms);
+        if (s != HJLO_OK) return s;
+        const bool blocks = ax.vblocks > 1;
+        out->lanes_per_line = ax.threads;        // one CTA per line or row block
+        out->segment_rows = 0;
+        out->lines_per_tile = 1;
+        out->threads = ax.threads;
+        out->smem_bytes = (int64_t)ax.smem;
+        out->tiles = ax.ntiles;
+        out->row_blocks = ax.vblocks;
+        out->block_rows = blocks ? ax.vR : 0;
+        out->line_points = blocks ? ax.vR + weff - 1 : N;
+        return HJLO_OK;
+    }
     hjlo_status s = shape_launch(ax, esize, algo == HJLO_ALGO_BRUTE ? KALGO_BRUTE : KALGO_MONGE, num_sms,
                                  (size_t)smem_optin);
     if (s != HJLO_OK) return s;
-    memset(out, 0, sizeof(*out));
     out->lanes_per_line = ax.lpl;
     out->segment_rows = ax.seg;
     out->lines_per_tile = ax.C;

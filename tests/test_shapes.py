@@ -71,6 +71,34 @@ def test_shape_invariants(algo, esize, num_sms, smem):
     assert ok > 100 and refused >= 1
 
 
+@pytest.mark.parametrize("num_sms,smem", [(152, 232448), (20, 101376)])
+def test_decomposition_shape_invariants(num_sms, smem):
+    """The decomposition pass: one CTA per line or row block, shared memory
+    within the CTA's, and for row blocks the blocks cover the line and a
+    block's span of sources (its rows + weff - 1) is no longer than the line,
+    as its gather (one wrap at most) needs."""
+    from paper_1210_4090_gb300 import hjlo
+    ok = 0
+    for N, lines, weff in _cases():
+        try:
+            s = hjlo.shape_query(N, lines, weff, 8, 3, num_sms, smem)
+        except hjlo.HjloError as e:
+            assert e.status == 6, e
+            continue
+        ok += 1
+        case = (N, lines, weff, s)
+        assert s["threads"] in (256, 1024) and 0 < s["smem_bytes"] <= smem, case
+        blocks, R, L = s["row_blocks"], s["block_rows"], s["line_points"]
+        assert s["tiles"] == lines * blocks, case
+        if blocks > 1:
+            assert 4 * weff <= N and R >= max(1, weff - 1), case
+            assert (blocks - 1) * R < N <= blocks * R, case
+            assert L == R + weff - 1 <= N, case
+        else:
+            assert R == 0 and L == N, case
+    assert ok > 50
+
+
 def test_shape_query_rejects_bad_arguments():
     from paper_1210_4090_gb300 import hjlo
     for args in [(0, 1, 1), (10, 0, 1), (10, 1, 0), (10, 1, 11)]:
@@ -80,4 +108,6 @@ def test_shape_query_rejects_bad_arguments():
     with pytest.raises(hjlo.HjloError):
         hjlo.shape_query(100, 1, 5, esize=2)
     with pytest.raises(hjlo.HjloError):
-        hjlo.shape_query(100, 1, 5, algo=3)
+        hjlo.shape_query(100, 1, 5, algo=4)
+    with pytest.raises(hjlo.HjloError):
+        hjlo.shape_query(100, 1, 5, esize=4, algo=3)     # the decomposition pass runs in binary64
