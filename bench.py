@@ -2,18 +2,20 @@
 """Throughput of the fully discrete Lax--Oleinik scheme on GB300.
 
 One benchmark step = one complete run of a workload from its initial data
-(default: grid1024, the 2D 1024^2 torus, W = 64, 1000 time steps, binary64)
-through the library's C ABI.  The metric is grid-point updates per second
+(default: cube256, the 3D 256^3 torus, W = 32, 500 time steps, binary64, the
+largest single-instance configuration) through the library's C ABI.  The metric is grid-point updates per second
 (points x time steps / time); every result is bit-exact against the CPU
 oracle (tests/test_gpu_parity.py).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload grid1024|cube256|line256] [--algo monge|brute]
+                    [--workload cube256|grid1024|line256|sweep512|adjoint512|paper1d|decomp|
+                                integral128|peaks] [--algo monge|brute]
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the plan's stream; before each timed step the state is reset to u0 and a
-256 MiB buffer is written to flush L2 (the 8 MiB grid of grid1024 is then
-L2-resident within a step, as in any run of that size).  Barrier and device
+256 MiB buffer is written to flush L2 (cube256's fields, 134 MB each, exceed
+L2; the 8 MiB grid of grid1024 is L2-resident within a step, as in any run of
+that size).  Barrier and device
 synchronisation on both sides of the timed region; the max over ranks is
 reported.  Under torchrun every rank runs an independent replica (the single
 grid does not shard: "replicas only"); value = all ranks' updates / max time.
@@ -23,7 +25,10 @@ page-locked host buffers, copies inside the timed region), roofline of the
 dominant kernel (the axis pass), the CPU oracle timed on a bounded sample of
 the same workload (cpu_baseline), SM clocks sampled during the timed region
 and the number of kernels launched.  --impl reference times the CPU oracle
-alone (the reference arm: the paper publishes no code).
+alone (the reference arm: the paper publishes no code), each step one bounded
+sample of the workload's time steps; steps and ms_per_step describe those
+samples.  --workload peaks measures the binary64 add rate (the brute-force
+pass's roofline) with a probe kernel.
 """
 from __future__ import annotations
 
@@ -57,9 +62,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-autotune", action="store_true", help="keep the cost model's launch shapes")
-    ap.add_argument("--workload", choices=["grid1024", "cube256", "line256", "sweep512", "adjoint512", "paper1d",
-                                           "decomp", "integral128"],
-                    default="grid1024")
+    ap.add_argument("--workload", choices=["cube256", "grid1024", "line256", "sweep512", "adjoint512", "paper1d",
+                                           "decomp", "integral128", "peaks"],
+                    default="cube256")
     ap.add_argument("--loop-instances", type=int, default=28,
                     help="sweep512: instances timed one plan at a time for the per-instance loop")
     ap.add_argument("--algo", choices=["monge", "brute", "auto"], default="monge")
@@ -173,7 +178,8 @@ class ClockSampler:
 
 def cpu_oracle_rate(p, budget_s):
     """The oracle as it stands on the host cores, on the first time steps of the
-    same workload; returns (updates/s, cores, sample description)."""
+    same workload (after one step timed alone to size the sample); returns
+    (updates/s, cores, sample description)."""
     from oracle import oracle as O
     cores = O.max_threads()
     t0 = time.perf_counter()
@@ -190,6 +196,11 @@ def cpu_oracle_rate(p, budget_s):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores.  Every step (warm-up
+    or timed) is one bounded sample -- the next consecutive time steps of the
+    workload, as many as fit the per-sample budget -- so steps and ms_per_step
+    describe exactly the work timed; value = updates / time over the timed
+    samples."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -197,23 +208,63 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_oracle_rate(p, per / 2)
-    rates, samples = [], []
-    for _ in range(args.steps):
-        r, cores, s = cpu_oracle_rate(p, per)
-        rates.append(r)
-        samples.append(s)
-    value = float(statistics.mean(rates))
+    # steps of the workload per sample, from a first step timed alone
+    t0 = time.perf_counter()
+    u = O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, 1)
+    first = time.perf_counter() - t0
+    k = int(max(1, min(max(1, (p.nsteps - 1) // max(1, args.steps + args.warmup)), per / max(first, 1e-9))))
+    done = 1
+    cores = O.max_threads()
+    secs, upd, samples = [], [], []
+    for i in range(args.warmup + args.steps):
+        if done + k > p.nsteps:                 # wrap: restart the run from u0 after its last step
+            u = O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, 1)
+            done = 1
+        t0 = time.perf_counter()
+        u = O.run(u, p.dx, p.h, p.P, p.W, p.V, k)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            secs.append(dt)
+            upd.append(p.npts * k)
+            samples.append("time steps %d..%d" % (done + 1, done + k))
+        done += k
+    value = float(sum(upd) / sum(secs))
+    sample = "%s %s, %d samples of %d consecutive time steps each (%s), %d OpenMP threads" % (
+        p.name, "x".join(map(str, p.shape)), args.steps, k, ", ".join(samples[:3]) + (", ..." if len(samples) > 3 else ""),
+        cores)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": p.npts * p.nsteps / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": float(np.mean(secs)) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": p.name, "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
-                       "h": p.h, "P": list(p.P), "parallelism": "host cores"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": samples[0]},
+                       "h": p.h, "P": list(p.P), "parallelism": "host cores",
+                       "step": "one sample of %d of the workload's %d time steps (%d updates)"
+                               % (k, p.nsteps, p.npts * k)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_peaks(args):
+    """The binary64 add rate of the device (hjlo_probe_fp64_add), the peak the
+    brute-force pass is measured against; best of K probes after W warm-ups."""
+    import torch
+    from paper_1210_4090_gb300 import hjlo
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    for _ in range(max(3, args.warmup)):
+        hjlo.probe_fp64_add(1 << 14)
+    rates = [hjlo.probe_fp64_add(1 << 16) for _ in range(args.steps)]
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    best = max(rates)
+    line = {"metric": "binary64 adds/s (probe)", "value": best, "unit": "adds/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "peaks", "kernel": "8 independent add chains per thread, 8 CTAs x 256 "
+                                                      "threads per SM, 2^16 adds per chain"},
+            "all": rates, "per_clock_per_sm_at_2070MHz": best / (sms * 2070.0e6)}
     print(json.dumps(line), flush=True)
 
 
@@ -545,12 +596,17 @@ def _time_run(plan, u0, V, nsteps, steps, warmup, tv=False):
 
 def run_decomp(args):
     """The paper's own fast convolution (Sec. 4, HJLO_ALGO_DECOMP) against the
-    monotone pass on the same runs: the paper's timed run (the pendulum of
-    Sec. 5.1 on 2^18 points, T = 8, eta = dx; one line in row blocks), the
-    pendulum on 2 x 4096 points at eta = 0, dx and 10 dx, and the 1024^2 grid
-    law for its first 100 steps at eta = 0.  Reports time, updates/s,
-    components per line and pass, and the relative sup-norm deviation from
-    the exact scheme (the monotone pass is bit-exact)."""
+    monotone pass on the same runs: the paper-size run (the pendulum of Sec.
+    5.1 on 2^18 points, T = 8; one line in row blocks) at eta = 0, where the
+    method is exact and the cut cannot change the result, and at the paper's
+    eta = dx with the approximate block-restart option (the whole 2^18-point
+    period does not fit one CTA, and at eta > 0 the method as the paper
+    defines it decomposes whole periods); the pendulum on 2 x 4096 points at
+    eta = 0, dx and 10 dx (the last two with block restarts, for the same
+    reason); the 1024^2 grid law for its first 100 steps at eta = 0 and dx
+    (whole lines).  Reports time, updates/s, components per line and pass,
+    and the relative sup-norm deviation from the exact scheme (the monotone
+    pass is bit-exact)."""
     import torch
     from paper_1210_4090_gb300 import hjlo
     rank, world, local = dist_env()
@@ -562,7 +618,10 @@ def run_decomp(args):
     big = WL.pendulum(2 ** 17)
     pend = WL.pendulum(4096)
     g = WL.grid1024(nsteps=100)
-    for p, etas in ((big, (big.dx[0],)), (pend, (0.0, pend.dx[0], 10 * pend.dx[0])), (g, (0.0,))):
+    plan_cases = ((big, ((0.0, False), (big.dx[0], True))),
+                  (pend, ((0.0, False), (pend.dx[0], True), (10 * pend.dx[0], True))),
+                  (g, ((0.0, False), (g.dx[0], False))))
+    for p, etas in plan_cases:
         u0 = torch.tensor(p.u0, device=dev)
         V = torch.tensor(p.V, device=dev)
         mono = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W, algo=hjlo.ALGO_MONGE)
@@ -570,24 +629,29 @@ def run_decomp(args):
         mono.close()
         ref = ref.cpu().numpy()
         lines_per_step = sum(p.npts // s for s in p.shape)
-        for eta in etas:
+        for eta, restart in etas:
             dec = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W, algo=hjlo.ALGO_DECOMP)
-            dec.set_tolerance(eta)
+            dec.set_tolerance(eta, restart_blocks=restart)
+            info = dec.info()
             ms_d, got = _time_run(dec, u0, V, p.nsteps, args.steps, args.warmup)
             cnt = dec.sync()
             dec.close()
             got = got.cpu().numpy()
             runs = max(3, args.warmup) + args.steps
             cases.append({"workload": p.name, "shape": list(p.shape), "nsteps": p.nsteps, "W": list(p.W),
-                          "eta": eta, "decomp_ms": ms_d, "monge_ms": ms_m,
+                          "eta": eta,
+                          "method": ("block restarts (approximate)" if restart and eta > 0
+                                     else "Sec. 4, one decomposition per period"),
+                          "row_blocks": info["row_blocks"], "decomp_ms": ms_d, "monge_ms": ms_m,
                           "decomp_updates_per_s": p.npts * p.nsteps / (ms_d * 1e-3),
                           "monge_updates_per_s": p.npts * p.nsteps / (ms_m * 1e-3),
                           "components_per_line_pass": cnt["components"] / (runs * p.nsteps * lines_per_step),
                           "rel_error_vs_exact": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))})
-    # the line's value: the paper's own timed run -- its approximate method
-    # (eta = dx) on the pendulum with 2^18 points to T = 8 -- whose reported
-    # ~19 min gives 262144 x 1634 updates / 1140 s (MATLAB, one 2.3 GHz
-    # laptop core: another machine, so the ratio is context)
+    # the line's value: the paper-size run (the pendulum with 2^18 points to
+    # T = 8) by the method as the paper defines it, at eta = 0 (exact); the
+    # paper timed its eta = dx variant at ~19 min, 262144 x 1634 updates /
+    # 1140 s (MATLAB, one 2.3 GHz laptop core: another machine and another
+    # tolerance, so the ratio is context)
     head = cases[0]
     paper = 262144 * 1634 / 1140.0
     line = {"metric": METRIC + " (decomposition method of Sec. 4)", "value": head["decomp_updates_per_s"],
@@ -595,9 +659,9 @@ def run_decomp(args):
             "ms_per_step": head["decomp_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["decomp_updates_per_s"] / paper, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "pendulum_2^18", "shape": head["shape"], "nsteps": head["nsteps"],
-                       "eta": "dx", "W": head["W"],
-                       "baseline": "the paper's ~19 min (MATLAB, 2.3 GHz laptop core) for this run: %.3g "
-                                   "updates/s" % paper,
+                       "eta": 0.0, "W": head["W"],
+                       "baseline": "the paper's ~19 min (MATLAB, 2.3 GHz laptop core) for this run at eta = dx: "
+                                   "%.3g updates/s" % paper,
                        "note": "comparison method; the headline path is the monotone pass"},
             "cases": cases}
     print(json.dumps(line), flush=True)
@@ -822,6 +886,8 @@ def main():
         run_decomp(args)
     elif args.workload == "integral128":
         run_integral(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

@@ -69,7 +69,7 @@ typedef enum {
     HJLO_ALGO_BRUTE = 1,    /* every window candidate evaluated in binary64 */
     HJLO_ALGO_MONGE = 2,    /* monotone-argmin search (see hjlo_plan_create) */
     HJLO_ALGO_DECOMP = 3    /* the paper's own fast convolution (Sec. 4): convex/concave
-                               decomposition of every line; see hjlo_plan_set_tolerance */
+                               decomposition of every line; see hjlo_plan_set_decomp */
 } hjlo_algo;
 
 /* Problem descriptor (one grid).  Sec. 2.3 eq. cost2 / eqconvol, Sec. 3.3. */
@@ -176,10 +176,31 @@ hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
  * component stays "convex" while the increase of its slopes, taken per unit
  * length ((u(i+1) - u(i)) / dx_a), is >= -eta (second differences
  * >= -eta * dx_a), so nearly affine stretches join fewer, longer components
- * (fewer components, larger values where the stretch is not convex).  Waits for the plan's stream;
- * later steps use the new value.  Errors: HJLO_EINVAL (another algorithm,
- * eta negative or not finite).
+ * (fewer components, larger values where the stretch is not convex).
+ *
+ * Each pass decomposes every line once over one period (its lifted span),
+ * as Sec. 4.2-4.3 take the function on the torus.  At eta = 0 the method is
+ * exact (every component is convex or concave: Theorems th:convex and
+ * th:ccc), so the result does not depend on where the cut starts and long
+ * or lonely contiguous lines run in row blocks, each cut on its own span.
+ * At eta > 0 the result does depend on the cut: with restart_blocks = 0 each
+ * line is decomposed whole (a line longer than one CTA holds, about 7000
+ * points, is HJLO_EUNSUPPORTED); restart_blocks = 1 runs such lines in row
+ * blocks that restart the decomposition at each block's first source, an
+ * approximation of the method with no counterpart in the paper: every
+ * output is still one candidate fl(u(y) + k(d)) of the scheme, so never
+ * below it, and a component of m pieces treated as convex adds at most
+ * eta dx_a m^2 to it (m <= block rows + window - 1).
+ *
+ * Waits for the plan's stream; later steps use the new settings (the
+ * plan's cached graph is rebuilt).  Errors: HJLO_EINVAL (another algorithm,
+ * eta negative or not finite, restart_blocks not 0 or 1), HJLO_EUNSUPPORTED
+ * (a line that does not fit whole at eta > 0 without restarts; the plan
+ * keeps its previous settings).
  */
+hjlo_status hjlo_plan_set_decomp(hjlo_plan *plan, double eta, int32_t restart_blocks);
+
+/* hjlo_plan_set_decomp(plan, eta, 0). */
 hjlo_status hjlo_plan_set_tolerance(hjlo_plan *plan, double eta);
 
 /*
@@ -409,6 +430,17 @@ typedef struct {
  */
 hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esize, int32_t algo, int32_t num_sms,
                              int64_t smem_optin, hjlo_shape_info *out);
+
+/*
+ * The binary64 add rate of the current device (a measurement helper, no
+ * counterpart in the paper: the brute-force pass is bound by one binary64
+ * add per window candidate).  Launches, on cuda_stream, a kernel whose
+ * threads run 8 independent add chains of `iters` adds each (grid: 8 CTAs of
+ * 256 threads per SM), once to warm up and once timed with CUDA events;
+ * *adds_per_s (host) receives adds / elapsed time.  Synchronous.  Errors:
+ * HJLO_EINVAL (iters outside 1..2^30, NULL output), HJLO_ECUDA.
+ */
+hjlo_status hjlo_probe_fp64_add(int64_t iters, void *cuda_stream, double *adds_per_s);
 
 /* Description of the last error on the calling thread ("" if none). */
 const char *hjlo_last_error(void);

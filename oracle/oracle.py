@@ -368,19 +368,16 @@ def decomp_line(src, k, eta: float = 0.0):
     return h[n:n + N], len(comps)
 
 
-def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_per_step: bool = False,
-               block_rows: int = 0):
+def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_per_step: bool = False):
     """nsteps of the scheme with every axis pass computed by the decomposition
     method (axis 0 first, then fl(m - fl(h V)) as in the scheme).  eta is the
     tolerance on the increase of the slopes (u(i+1) - u(i)) / dx along the
     line, as the slopes of Sec. 4.1 are taken per unit length: on axis a the
-    second differences are compared with -fl(eta * dx_a).  The decomposition
-    of a periodic line has to start somewhere; it starts at the first source
-    of the line's lifted span, or, with block_rows = R > 0, the last axis's
-    lines are taken in blocks of R outputs and each block's span (R + n
-    sources) is decomposed on its own (the same method, restarted at each
-    block; at eta = 0 the result does not depend on it).  Returns (u, total
-    number of components over all lines, blocks and passes)."""
+    second differences are compared with -fl(eta * dx_a).  Each line is
+    decomposed once per pass (Sec. 4.2-4.3 take the function over one period
+    of the torus): the decomposition runs over the line's lifted span, from
+    its first source.  Returns (u, total number of components over all lines
+    and passes)."""
     u = np.array(u0, dtype=np.float64, copy=True)
     shape = u.shape
     ndim = u.ndim
@@ -394,14 +391,10 @@ def decomp_run(u0, dx, h, P, W, V=None, nsteps: int = 1, eta: float = 0.0, *, V_
             n = dhi - dlo
             v = np.moveaxis(u, a, -1)
             out = np.empty_like(v)
-            R = int(block_rows) if (block_rows and a == ndim - 1) else N
             for idx in np.ndindex(*v.shape[:-1]):
-                line = v[idx]
-                for r0 in range(0, N, R):
-                    src = line[(r0 + np.arange(R + n) - dhi) % N]
-                    part, c = decomp_line(src, k, float(eta) * float(dxv[a]))
-                    out[idx][r0:r0 + R] = part[:N - r0]
-                    ncomp += c
+                src = v[idx][(np.arange(N + n) - dhi) % N]
+                out[idx], c = decomp_line(src, k, float(eta) * float(dxv[a]))
+                ncomp += c
             u = np.ascontiguousarray(np.moveaxis(out, -1, a))
         if V is not None:
             Vs = np.asarray(V, dtype=np.float64)

@@ -619,23 +619,44 @@ hjlo_status hjlo_plan_autotune(hjlo_plan *p, const void *u, const double *V, int
     return HJLO_OK;
 }
 
-hjlo_status hjlo_plan_set_tolerance(hjlo_plan *p, double eta)
+hjlo_status hjlo_plan_set_decomp(hjlo_plan *p, double eta, int32_t restart_blocks)
 {
     hjlo_status s = check_plan(p);
     if (s != HJLO_OK) return s;
     if (p->algo != HJLO_ALGO_DECOMP) return set_error(HJLO_EINVAL, "the tolerance applies to HJLO_ALGO_DECOMP plans");
     if (!(eta >= 0.0) || !std::isfinite(eta)) return set_error(HJLO_EINVAL, "eta must be finite and >= 0");
+    if (restart_blocks != 0 && restart_blocks != 1) return set_error(HJLO_EINVAL, "restart_blocks must be 0 or 1");
     if ((s = set_device(p)) != HJLO_OK) return s;
+    DeviceFacts df;
+    if ((s = device_facts(df)) != HJLO_OK) return s;
+    // launch shapes first (nothing changes if one does not fit): at eta = 0
+    // the result does not depend on where a line's cut starts, so long or
+    // lonely lines keep their row blocks; at eta > 0 a period is decomposed
+    // whole unless the caller asked for restarts at each block
+    const bool blocks_ok = (eta == 0.0) || restart_blocks;
+    AxisPlan shaped[HJLO_MAX_DIM];
+    for (int a = 0; a < p->ndim; ++a) {
+        shaped[a] = p->ax[a];
+        if ((s = shape_decomp(shaped[a], df.smem_optin, df.num_sms, blocks_ok)) != HJLO_OK) return s;
+        if (shaped[a].vblocks > 1 && !p->d_scratch)
+            return set_error(HJLO_EUNSUPPORTED, "row blocks need the plan's scratch, which this plan has not");
+    }
     // launches already enqueued keep their own copy of the parameters; the
     // cached graph holds the old value and is rebuilt on next use
     cudaError_t e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
     // slopes per unit length (Sec. 4.1): the second differences along axis a
     // are compared with -eta * dx_a
-    for (int a = 0; a < p->ndim; ++a) p->ax[a].eta = eta * p->desc.dx[a];
+    for (int a = 0; a < p->ndim; ++a) {
+        p->ax[a] = shaped[a];
+        p->ax[a].eta = eta * p->desc.dx[a];
+    }
+    p->decomp_restart = restart_blocks;
     destroy_graph(p);
     return HJLO_OK;
 }
+
+hjlo_status hjlo_plan_set_tolerance(hjlo_plan *p, double eta) { return hjlo_plan_set_decomp(p, eta, 0); }
 
 hjlo_status hjlo_sync(hjlo_plan *p, hjlo_counters *out)
 {

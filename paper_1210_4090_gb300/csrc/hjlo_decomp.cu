@@ -6,8 +6,13 @@
 // lm:simplif / Theorem th:ccc / Algorithm 2 for a concave one), and the
 // output is the minimum over components (Sec. 4.3 step 3).
 //
-// One CTA per line (or row block of a long or lonely contiguous line, each
-// decomposed on its own span).  The lifted source line and the kernel are staged in
+// One CTA per line.  A decomposition runs over one period of the line (its
+// lifted span), as Sec. 4.2-4.3 take it; where the result cannot depend on
+// where the cut starts (eta = 0: every component is exactly convex or
+// concave and the method is exact), or where the caller asks for it
+// (hjlo_plan_set_decomp's approximate restart option), a long or lonely
+// contiguous line runs in row blocks, each block decomposing its own span.
+// The lifted source line and the kernel are staged in
 // shared memory; the slope-increment kinds of all interior points are
 // classified in parallel into two bitmaps; one thread walks the bitmaps to
 // cut the components greedily (the cut is a left-to-right dependency chain,
@@ -406,7 +411,7 @@ hjlo_status decomp_allow_smem()
     return e == cudaSuccess ? HJLO_OK : cuda_error(e, "cudaFuncSetAttribute(decomp)");
 }
 
-hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms)
+hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool blocks_ok)
 {
     ax.algo = KALGO_DECOMP;
     ax.layout = (ax.inner == 1) ? LAYOUT_CONTIG : LAYOUT_STRIDED;
@@ -415,16 +420,17 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms)
     ax.vNp = 0;
     if (ax.weff >= 3 && !(ax.curv > 0))
         return set_error(HJLO_EPRECOND, "the decomposition pass needs a strictly convex kernel table");
-    // Row blocks for a contiguous axis, as for the other passes: when the
-    // window is at most a quarter of the line and either a whole line does
-    // not fit or the axis has fewer lines than half the SMs.  Each block is
-    // decomposed on its own span (the cut restarts at the block's first
-    // source).  Blocks hold one SM's share of the rows, at least weff - 1
-    // (the span is at most twice the rows: on the 2^18-point pendulum at
-    // eta = dx, 161 blocks of 1636 rows ran 22 % faster than 81 of 3272).
+    // Row blocks for a contiguous axis (blocks_ok), as for the other passes:
+    // when the window is at most a quarter of the line and either a whole
+    // line does not fit or the axis has fewer lines than half the SMs.  Each
+    // block is decomposed on its own span (the cut restarts at the block's
+    // first source).  Blocks hold one SM's share of the rows, at least
+    // weff - 1 (the span is at most twice the rows: on the 2^18-point
+    // pendulum at eta = dx, 161 blocks of 1636 rows ran 22 % faster than 81
+    // of 3272).
     const long long N = ax.N, w = ax.weff, lines = ax.outer;
     const bool fits = decomp_smem(ax, N, nullptr) <= smem_optin;
-    if (ax.inner == 1 && 4 * w <= N && (!fits || 2 * lines < num_sms)) {
+    if (blocks_ok && ax.inner == 1 && 4 * w <= N && (!fits || 2 * lines < num_sms)) {
         long long vR = std::max(std::max(1LL, w - 1), (N * lines + num_sms - 1) / num_sms);
         const ShapeHints hint = env_hints();
         if (hint.block_rows > 0) vR = std::max(hint.block_rows, std::max(1LL, w - 1));
@@ -438,7 +444,12 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms)
     const long long rowsN = (ax.vblocks > 1) ? ax.vR : N;
     ax.smem = decomp_smem(ax, rowsN, nullptr);
     if (ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))
-        return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit the decomposition pass", ax.N);
+        return set_error(HJLO_EUNSUPPORTED,
+                         blocks_ok ? "a line of %lld points does not fit the decomposition pass"
+                                   : "a line of %lld points does not fit one CTA: with eta > 0 the decomposition of a "
+                                     "period needs the whole line (hjlo_plan_set_decomp's restart option runs it in "
+                                     "row blocks, approximately)",
+                         ax.N);
     ax.ntiles = ax.inner * ax.outer * ax.vblocks;
     // one CTA per line: few lines (a 1D problem) get 32 warps each to hide
     // the latency of their components' searches; many lines get 8 warps

@@ -121,7 +121,9 @@ hjlo_status kern_batch_f32_strided(const AxisPlan &ax, const BatchItem *items, c
 
 // The paper's decomposition method as an axis pass (hjlo_decomp.cu).
 hjlo_status decomp_allow_smem();
-hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms);
+// blocks_ok: a contiguous axis may run in row blocks (each decomposed on its
+// own span); false: whole lines only (EUNSUPPORTED when a line does not fit).
+hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool blocks_ok = true);
 hjlo_status launch_decomp(const AxisPlan &ax, const void *src, void *dst, const double *hv, double hv_scale,
                           unsigned long long *counters, int *flags, cudaStream_t st);
 
@@ -153,6 +155,7 @@ struct hjlo_plan {
     int ndim = 1;
     int dtype = HJLO_F64;
     int algo = HJLO_ALGO_MONGE;
+    int decomp_restart = 0;                    // DECOMP: row blocks restart the cut at eta > 0 (approximate)
     long long npts = 1;
     int esize = 8;
     cudaStream_t stream = nullptr;

@@ -82,6 +82,8 @@ _SIGS = [
     ("hjlo_plan_destroy", _i32, [_vp]),
     ("hjlo_plan_info", _i32, [_vp, ctypes.POINTER(Facts)]),
     ("hjlo_plan_set_tolerance", _i32, [_vp, _f64]),
+    ("hjlo_plan_set_decomp", _i32, [_vp, _f64, _i32]),
+    ("hjlo_probe_fp64_add", _i32, [_i64, _vp, _vp]),
     ("hjlo_plan_autotune", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(TuneReport)]),
     ("hjlo_integral_create", _i32, [ctypes.POINTER(Desc), _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp,
                                     ctypes.POINTER(_vp)]),
@@ -123,6 +125,13 @@ def shape_query(N, lines, weff, esize=8, algo=ALGO_MONGE, num_sms=152, smem_opti
     _check(lib().hjlo_shape_query(int(N), int(lines), int(weff), int(esize), int(algo), int(num_sms),
                                   int(smem_optin), ctypes.byref(out)), "hjlo_shape_query")
     return {f: getattr(out, f) for f, _ in ShapeInfo._fields_}
+
+
+def probe_fp64_add(iters: int = 1 << 16, stream=None) -> float:
+    """The device's binary64 add rate in adds/s (hjlo_probe_fp64_add)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().hjlo_probe_fp64_add(int(iters), stream, ctypes.byref(out)), "hjlo_probe_fp64_add")
+    return float(out.value)
 
 
 def lib() -> ctypes.CDLL:
@@ -255,9 +264,12 @@ class Plan:
                "hjlo_plan_autotune")
         return r.as_dict()
 
-    def set_tolerance(self, eta: float):
-        """Convexity tolerance of an ALGO_DECOMP plan (Sec. 4.4)."""
-        _check(lib().hjlo_plan_set_tolerance(self._h, float(eta)), "hjlo_plan_set_tolerance")
+    def set_tolerance(self, eta: float, restart_blocks: bool = False):
+        """Convexity tolerance of an ALGO_DECOMP plan (Sec. 4.4).  Each line is
+        decomposed once per pass; restart_blocks=True lets lines too long for
+        one CTA run in row blocks that restart the decomposition (an
+        approximation, see hjlo_plan_set_decomp)."""
+        _check(lib().hjlo_plan_set_decomp(self._h, float(eta), 1 if restart_blocks else 0), "hjlo_plan_set_decomp")
 
     def info(self) -> dict:
         f = Facts()

@@ -122,28 +122,25 @@ def test_error_grows_with_eta_and_components_shrink():
     assert errs[-1] >= errs[0]
 
 
-def test_blocks_at_zero_tolerance_equal_the_scheme():
+def test_zero_tolerance_equals_the_scheme_for_any_start():
     """At eta = 0 every component is exactly convex or concave and the method
-    is exact, so restarting the decomposition at each block of rows changes
-    nothing: equal to the scheme (and to the whole-line decomposition)."""
+    is exact (Theorem th:convex, Theorem th:ccc), so the result does not
+    depend on where the decomposition of the periodic line starts: lines
+    rotated before the pass give the scheme's values rotated."""
     N, W, h = 300, 12, 0.01
     x = np.arange(N) / N
     rng = np.random.default_rng(5)
     u0 = 0.3 * np.sin(6 * np.pi * x) + 0.01 * rng.normal(size=N)
-    V = 0.1 * np.cos(2 * np.pi * x)
-    ref = O.run(u0, 1.0 / N, h, 0.2, W, V, 3)
-    for R in (24, 40, 77, 300):
-        got, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, V, 3, 0.0, block_rows=R)
-        assert np.array_equal(got.view(np.int64), ref.view(np.int64)), R
-    whole, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, V, 3, 0.0)
-    assert np.array_equal(whole.view(np.int64), ref.view(np.int64))
+    ref = O.run(u0, 1.0 / N, h, 0.2, W, None, 1)
+    for shift in (0, 24, 77, 151):
+        got, _ = O.decomp_run(np.roll(u0, shift), 1.0 / N, h, 0.2, W, None, 1, 0.0)
+        assert np.array_equal(np.roll(got, -shift).view(np.int64), ref.view(np.int64)), shift
 
 
-@pytest.mark.parametrize("R", [24, 77, 300])
-def test_blocks_with_tolerance_stay_candidates(R):
-    """With eta > 0 and the decomposition restarted at each block of rows
-    (A27), every output is still one candidate of the scheme, so never below
-    the exact scheme's value, and the gap shrinks with eta."""
+def test_tolerance_outputs_stay_candidates():
+    """With eta > 0 every output is still one candidate of the scheme (a value
+    f(i) + g(j) of the components' convolutions), so never below the exact
+    scheme's value, and the gap grows with eta."""
     N, W, h = 300, 12, 0.01
     x = np.arange(N) / N
     rng = np.random.default_rng(6)
@@ -151,7 +148,7 @@ def test_blocks_with_tolerance_stay_candidates(R):
     exact = O.run(u0, 1.0 / N, h, 0.2, W, None, 1)
     gaps = []
     for eta in (0.5, 5.0, 50.0):
-        got, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, None, 1, eta, block_rows=R)
+        got, _ = O.decomp_run(u0, 1.0 / N, h, 0.2, W, None, 1, eta)
         assert np.all(got >= exact), eta
         gaps.append(float(np.max(got - exact)))
     assert gaps[0] <= gaps[1] <= gaps[2], gaps

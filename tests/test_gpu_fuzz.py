@@ -79,23 +79,24 @@ def _decomp_case(i):
 @pytest.mark.parametrize("i", range(NDECOMP))
 def test_random_geometry_decomposition(i):
     """The paper's Sec. 4 method on random geometries: bit for bit against the
-    oracle's version of the method (restarted at the plan's row blocks), the
-    same number of components."""
+    oracle's version of the method, with the same number of components when
+    eta > 0 (at eta = 0 the values are the scheme's whatever the cut, and
+    long or lonely lines may run in row blocks)."""
     from paper_1210_4090_gb300 import hjlo
     shape, dx, h, P, W, u0, V, n, eta = _decomp_case(i)
     try:
         plan = hjlo.Plan(shape, dx, h, P, W, algo=hjlo.ALGO_DECOMP)
+        if eta:
+            plan.set_tolerance(eta)
     except hjlo.HjloError as e:            # a non-strictly-convex table or a line too long
         assert e.status in (4, 6), e
         return
-    R = plan.info()["block_rows"][-1]
-    if eta:
-        plan.set_tolerance(eta)
     u = torch.tensor(u0, device="cuda")
     plan.run(u, None if V is None else torch.tensor(V, device="cuda"), n)
     cnt = plan.sync()
     plan.close()
-    ref, ncomp = O.decomp_run(u0, dx, h, P, W, V, n, eta, block_rows=R)
+    ref, ncomp = O.decomp_run(u0, dx, h, P, W, V, n, eta)
     assert cnt["error_flags"] == 0
     assert np.array_equal(u.cpu().numpy().view(np.int64), ref.view(np.int64)), (shape, W, P, eta)
-    assert cnt["components"] == ncomp
+    if eta:
+        assert cnt["components"] == ncomp
