@@ -399,9 +399,25 @@ hjlo_status hjlo_integral_destroy(hjlo_integral *plan);
  * attributes; make that first call before any stream capture.  The kernel
  * tables are copied from host (pageable) memory, which orders the copy after
  * earlier work on the stream.  Results equal hjlo_step's bit for bit.
+ * Errors found on the device (a bounded wait that ran out, a failed
+ * precondition) cannot be returned by this asynchronous call: they collect
+ * in the array's error word, which no step clears; hjlo_noalloc_status
+ * reports and clears them.  Argument errors are returned at once.
  */
 hjlo_status hjlo_step_noalloc(const hjlo_desc *desc, void *cuda_stream, const void *u_in, void *u_out,
                               const double *V);
+
+/*
+ * The device status of hjlo_step_noalloc calls on the current device (no
+ * counterpart in the paper).  Waits for cuda_stream, copies the static
+ * array's counters of the most recent step and its error word into *out
+ * (host, may be NULL; fields a step does not keep are 0), clears the error
+ * word and returns HJLO_ETIMEOUT (a bounded device wait gave up: that
+ * step's output is incomplete) or HJLO_EPRECOND if any step since the
+ * previous status call raised one, else HJLO_OK.  Allocates nothing.
+ * Errors: HJLO_ECUDA.
+ */
+hjlo_status hjlo_noalloc_status(void *cuda_stream, hjlo_counters *out);
 
 /* Launch shape of one axis pass (host struct; see hjlo_shape_query). */
 typedef struct {

@@ -48,6 +48,22 @@ hjlo_status cuda_error(cudaError_t e, const char *what);
 
 // Host kernel tables of eq. cost2 for one axis (binary64, fixed order).
 double kernel_entry(long long d, double dx, double h, double P);
+
+// The window of displacements [lo, hi] of one axis (eq. los, Sec. 4.2: centred
+// on the kernel's largest minimiser c, or the N displacements of the full
+// torus window) and k[c].
+struct AxisWindow {
+    long long lo = 0, hi = 0, centre = 0, weff = 1;
+    double kmin = 0.0;
+};
+hjlo_status resolve_window(long long N, double dx, double h, double P, long long W, AxisWindow &win);
+
+// The reversed table k64[t] = k[hi - t], t < weff, into a caller buffer of at
+// least win.weff doubles, and the axis facts (window, hoff, kmax, curvature).
+void fill_axis_table(long long N, double dx, double h, double P, const AxisWindow &win, AxisPlan &ax, double *k64);
+
+// resolve_window + fill_axis_table into a malloc'ed table (*kr64_host, freed
+// by the caller).
 hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W, AxisPlan &ax,
                          double **kr64_host);
 

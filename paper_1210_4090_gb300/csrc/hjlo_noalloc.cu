@@ -16,7 +16,9 @@
 // The array is shared by every call: a call overwrites the previous call's
 // tables and clears the counters before its kernels run.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads without
-// ordering) race on the array.
+// ordering) race on the array.  The device error word (a bounded wait that
+// ran out, a failed precondition) is not cleared by a step: it collects the
+// flags of every step until hjlo_noalloc_status reads and clears it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -69,58 +71,17 @@ hjlo_status scratch_for_current_device(NoAllocScratch **out)
 }
 
 // Window and reversed kernel table of one axis into a caller-provided buffer
-// (same definitions as a plan's tables; no allocation).
+// of `cap` doubles (the plans' resolver; no allocation).
 hjlo_status table_into(long long N, double dx, double h, double P, long long W, AxisPlan &ax, double *kr64,
                        int cap)
 {
-    double ds = P * h / dx;
-    if (!(std::fabs(ds) < 1.0e9)) return set_error(HJLO_EUNSUPPORTED, "kernel minimiser P*h/dx out of range");
-    long long base = (long long)std::floor(ds);
-    long long c = base - 5;
-    double kc = kernel_entry(c, dx, h, P);
-    for (long long d = base - 4; d <= base + 6; ++d) {
-        double kd = kernel_entry(d, dx, h, P);
-        if (kd <= kc) { kc = kd; c = d; }
-    }
-    long long lo, hi;
-    if (W > 0 && 2 * W + 1 < N) {
-        lo = c - W;
-        hi = c + W;
-    } else {
-        if (N > cap) return set_error(HJLO_EUNSUPPORTED, "full window of %lld exceeds the no-allocation limit %d", N, cap);
-        lo = hi = c;
-        while (hi - lo + 1 < N) {
-            if (kernel_entry(lo - 1, dx, h, P) < kernel_entry(hi + 1, dx, h, P)) --lo; else ++hi;
-        }
-    }
-    const long long weff = hi - lo + 1;
-    if (weff > cap)
+    AxisWindow win;
+    hjlo_status s = resolve_window(N, dx, h, P, W, win);
+    if (s != HJLO_OK) return s;
+    if (win.weff > cap)
         return set_error(HJLO_EUNSUPPORTED, "window of %lld displacements exceeds the no-allocation limit %d",
-                         weff, cap);
-    if (lo < -(1LL << 30) || hi > (1LL << 30)) return set_error(HJLO_EUNSUPPORTED, "displacements out of int32 range");
-    double kmax = 0.0;
-    for (long long t = 0; t < weff; ++t) {
-        kr64[t] = kernel_entry(hi - t, dx, h, P);
-        kmax = std::max(kmax, std::fabs(kr64[t]));
-    }
-    double curv = INFINITY;
-    for (long long t = 1; t + 1 < weff; ++t) {
-        double a = kr64[t - 1] - kr64[t];
-        double b = kr64[t] - kr64[t + 1];
-        double s = a - b;
-        curv = std::min(curv, s - 0x1p-52 * (std::fabs(a) + std::fabs(b) + std::fabs(s)));
-    }
-    ax.N = N;
-    ax.dlo = lo;
-    ax.dhi = hi;
-    ax.centre = c;
-    ax.weff = (int)weff;
-    long long ho = (-hi) % N;
-    if (ho < 0) ho += N;
-    ax.hoff = (int)ho;
-    ax.kmin = kc;
-    ax.kmax = kmax;
-    ax.curv = curv;
+                         win.weff, cap);
+    fill_axis_table(N, dx, h, P, win, ax, kr64);
     return HJLO_OK;
 }
 
@@ -181,6 +142,7 @@ extern "C" hjlo_status hjlo_step_noalloc(const hjlo_desc *d, void *cuda_stream, 
         // whole lines only: row blocks cannot run in place and this step owns no scratch
         if ((s = shape_launch(ax[a], esize, algo, df.num_sms, df.smem_optin, 1, nullptr, false)) != HJLO_OK)
             return s;
+        apply_test_knobs(ax[a]);
         ax[a].d_kr64 = scr->kr64[a];
         // synchronous with respect to this host buffer for pageable memory
         cudaError_t e = cudaMemcpyAsync(ax[a].d_kr64, host_tab, sizeof(double) * ax[a].weff,
@@ -189,13 +151,45 @@ extern "C" hjlo_status hjlo_step_noalloc(const hjlo_desc *d, void *cuda_stream, 
     }
     unsigned long long *counters = scr->counters;
     int *flags = reinterpret_cast<int *>(scr->counters + CNT_N);
-    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * kCounterWords, st);
+    // counters start at zero for this step; the error word keeps earlier
+    // steps' flags until hjlo_noalloc_status reads it
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * CNT_N, st);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(no-allocation counters)");
     for (int a = 0; a < d->ndim; ++a) {
         const bool last = (a == d->ndim - 1);
         s = launch_pass(ax[a], d->dtype, a == 0 ? u_in : u_out, u_out, last ? V : nullptr, last && V ? d->h : 0.0,
                         nullptr, counters, flags, st);
         if (s != HJLO_OK) return s;
+    }
+    return HJLO_OK;
+}
+
+extern "C" hjlo_status hjlo_noalloc_status(void *cuda_stream, hjlo_counters *out)
+{
+    NoAllocScratch *scr = nullptr;
+    hjlo_status s = scratch_for_current_device(&scr);
+    if (s != HJLO_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned long long c[kCounterWords];
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c, scr->counters, sizeof(c), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "no-allocation status copy");
+    int flags = 0;
+    memcpy(&flags, &c[CNT_N], sizeof(int));
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->exact_rescans = (int64_t)c[CNT_RESCAN];
+        out->brute_fallback_lines = (int64_t)c[CNT_FALLBACK];
+        out->window_edge_hits = (int64_t)c[CNT_EDGE];
+        out->error_flags = flags;
+    }
+    if (flags) {
+        e = cudaMemsetAsync(&scr->counters[CNT_N], 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_error(e, "no-allocation status clear");
+        if (flags & FLAG_TIMEOUT) return set_error(HJLO_ETIMEOUT, "a bounded device wait of a no-allocation step gave up");
+        return set_error(HJLO_EPRECOND, "a numerical precondition of a no-allocation step failed");
     }
     return HJLO_OK;
 }

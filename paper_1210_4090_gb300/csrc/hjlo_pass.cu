@@ -62,10 +62,8 @@ double kernel_entry(long long d, double dx, double h, double P)
     return h * L;
 }
 
-hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W, AxisPlan &ax,
-                         double **kr64_host)
+hjlo_status resolve_window(long long N, double dx, double h, double P, long long W, AxisWindow &win)
 {
-    *kr64_host = nullptr;
     double ds = P * h / dx;
     if (!(std::fabs(ds) < 1.0e9)) return set_error(HJLO_EUNSUPPORTED, "kernel minimiser P*h/dx out of range");
     long long base = (long long)std::floor(ds);
@@ -85,11 +83,20 @@ hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W
             if (kernel_entry(lo - 1, dx, h, P) < kernel_entry(hi + 1, dx, h, P)) --lo; else ++hi;
         }
     }
-    long long weff = hi - lo + 1;
+    const long long weff = hi - lo + 1;
     if (weff > 65535) return set_error(HJLO_EUNSUPPORTED, "window of %lld displacements exceeds 65535", weff);
     if (lo < -(1LL << 30) || hi > (1LL << 30)) return set_error(HJLO_EUNSUPPORTED, "displacements out of int32 range");
-    double *k64 = (double *)malloc(sizeof(double) * weff);
-    if (!k64) return set_error(HJLO_ENOMEM, "host table allocation");
+    win.lo = lo;
+    win.hi = hi;
+    win.centre = c;
+    win.kmin = kc;
+    win.weff = weff;
+    return HJLO_OK;
+}
+
+void fill_axis_table(long long N, double dx, double h, double P, const AxisWindow &win, AxisPlan &ax, double *k64)
+{
+    const long long lo = win.lo, hi = win.hi, weff = win.weff;
     double kmax = 0.0;
     for (long long t = 0; t < weff; ++t) {
         double k = kernel_entry(hi - t, dx, h, P);
@@ -109,14 +116,26 @@ hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W
     ax.N = N;
     ax.dlo = lo;
     ax.dhi = hi;
-    ax.centre = c;
+    ax.centre = win.centre;
     ax.weff = (int)weff;
     long long ho = (-hi) % N;
     if (ho < 0) ho += N;
     ax.hoff = (int)ho;
-    ax.kmin = kc;
+    ax.kmin = win.kmin;
     ax.kmax = kmax;
     ax.curv = curv;
+}
+
+hjlo_status resolve_axis(long long N, double dx, double h, double P, long long W, AxisPlan &ax,
+                         double **kr64_host)
+{
+    *kr64_host = nullptr;
+    AxisWindow win;
+    hjlo_status s = resolve_window(N, dx, h, P, W, win);
+    if (s != HJLO_OK) return s;
+    double *k64 = (double *)malloc(sizeof(double) * win.weff);
+    if (!k64) return set_error(HJLO_ENOMEM, "host table allocation");
+    fill_axis_table(N, dx, h, P, win, ax, k64);
     *kr64_host = k64;
     return HJLO_OK;
 }

@@ -84,6 +84,7 @@ _SIGS = [
     ("hjlo_plan_set_tolerance", _i32, [_vp, _f64]),
     ("hjlo_plan_set_decomp", _i32, [_vp, _f64, _i32]),
     ("hjlo_probe_fp64_add", _i32, [_i64, _vp, _vp]),
+    ("hjlo_noalloc_status", _i32, [_vp, _vp]),
     ("hjlo_plan_autotune", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(TuneReport)]),
     ("hjlo_integral_create", _i32, [ctypes.POINTER(Desc), _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp,
                                     ctypes.POINTER(_vp)]),
@@ -207,6 +208,19 @@ def step_noalloc(u_in, u_out, V, shape, dx, h, P, W=0, dtype=F64, algo=ALGO_AUTO
     _check(lib().hjlo_step_noalloc(ctypes.byref(desc), _vp(_stream_handle(stream)), _vp(u_in.data_ptr()),
                                    _vp(u_out.data_ptr()), vp), "hjlo_step_noalloc")
     return u_out
+
+
+def noalloc_status(stream=None) -> dict:
+    """Device status of the no-allocation steps (hjlo_noalloc_status): waits for
+    the stream, returns the counters of the most recent step and raises
+    HjloError (HJLO_ETIMEOUT / HJLO_EPRECOND) if a step since the previous
+    call raised a device error flag (the flag is cleared)."""
+    c = Counters()
+    st = lib().hjlo_noalloc_status(_vp(_stream_handle(stream)), ctypes.byref(c))
+    res = {"exact_rescans": c.exact_rescans, "brute_fallback_lines": c.brute_fallback_lines,
+           "error_flags": c.error_flags, "window_edge_hits": c.window_edge_hits}
+    _check(st, "hjlo_noalloc_status")
+    return res
 
 
 class Plan:

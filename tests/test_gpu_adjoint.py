@@ -141,3 +141,74 @@ def test_autograd_function():
     assert np.array_equal(u0t.grad.cpu().numpy(), r0)
     assert np.array_equal(Vt.grad.cpu().numpy(), rV)
     assert np.allclose(Pt.grad.numpy(), rP, rtol=1e-11)
+
+
+def test_adjoint512_law_finite_differences_P_and_64_coefficients():
+    """The adjoint workload's law on a 64^2 copy (checkpoint every 25 steps):
+    central differences (eps = 1e-6) of loss = mean (u^n - u^0)/(n h) in P
+    and in each of the 64 coefficients of V against the adjoint's dJ/dP and
+    the projected coefficient gradients.
+
+    u^n(x) is a minimum over discrete paths of functions affine in (P, V)
+    (k[d] is affine in P, the potential term in V), so the loss is concave
+    and piecewise linear, and the adjoint's gradient -- the slope of the path
+    the recorded argmins select -- is a supergradient: the one-sided
+    quotients bracket it, (J(+eps) - J)/eps <= g <= (J - J(-eps))/eps, for
+    every coordinate whatever argmins the bracket flips (checked up to the
+    runs' rounding).  Where no argmin of any step changes in the bracket the
+    central quotient equals g up to rounding (1e-6 relative); with a few
+    near-ties flipped it stays within the survey's 1e-5 relative for most
+    coordinates."""
+    from paper_1210_4090_gb300 import hjlo
+    p = WL.adjoint512(N=64, nsteps=120, W=4)
+    n, S, eps = p.nsteps, 25, 1e-6
+    B = WL.adjoint_basis(64)
+    coef = p.extra["coef"]
+    ub = np.full(p.shape, 1.0 / (p.npts * n * p.h))
+    t = lambda a: torch.tensor(a, device="cuda")
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W)
+    _, gP, gV, _ = plan.adjoint(t(p.u0), t(p.V), n, t(ub), S)
+    gc = plan.project(gV, t(B)).cpu().numpy()
+    gP = gP.cpu().numpy()
+    plan.close()
+
+    def loss(P_, c_):
+        pl = hjlo.Plan(p.shape, p.dx, p.h, P_, p.W)
+        u = t(p.u0)
+        Vt = t(np.tensordot(c_, B, axes=(0, 0)))
+        am = torch.empty((n, 2 * p.npts), dtype=torch.int32, device="cuda")
+        for k in range(n):
+            pl.step(u, u, Vt, argmin=am[k])
+        pl.close()
+        un = u.cpu().numpy()
+        return float(np.mean(un - p.u0) / (n * p.h)), am.cpu().numpy()
+
+    J0, am0 = loss(p.P, coef)
+    exact = close = 0
+    flips = []
+    tol_slope = 1e-7                 # rounding of the runs (|J| ~ 0.1, ~1e-14) over eps
+    coords = [("P", a) for a in range(2)] + [("c", k) for k in range(64)]
+    for kind, i in coords:
+        if kind == "P":
+            Pp, Pm = list(p.P), list(p.P)
+            Pp[i] += eps
+            Pm[i] -= eps
+            (jp, amp), (jm, amm) = loss(Pp, coef), loss(Pm, coef)
+            g = gP[i]
+        else:
+            cp, cm = coef.copy(), coef.copy()
+            cp[i] += eps
+            cm[i] -= eps
+            (jp, amp), (jm, amm) = loss(p.P, cp), loss(p.P, cm)
+            g = gc[i]
+        s_plus, s_minus = (jp - J0) / eps, (J0 - jm) / eps
+        assert s_plus <= g + tol_slope and g <= s_minus + tol_slope, (kind, i, s_plus, g, s_minus)
+        fd = (jp - jm) / (2 * eps)
+        nflip = int(np.count_nonzero(amp != am0) + np.count_nonzero(amm != am0))
+        flips.append(nflip)
+        if nflip == 0:
+            assert abs(fd - g) <= 1e-6 * (abs(g) + 1e-3), (kind, i, fd, g)
+            exact += 1
+        if abs(fd - g) <= 1e-5 * (abs(g) + 1e-3):
+            close += 1
+    assert close >= 0.75 * len(coords), (close, exact, sorted(flips)[:10])
