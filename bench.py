@@ -280,10 +280,12 @@ def run_sweep(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1210_4090_gb300 import hjlo
 
-    # instances are independent: rank r takes every world-th instance
+    # instances are independent: each rank takes its LPT share of the work
+    # (N_i^2 points per instance); the H-bar rows are gathered at the end
     from paper_1210_4090_gb300 import dist as D
     allp = WL.sweep512()
-    probs = D.shard(allp, rank, world)
+    idx = D.shard_indices(len(allp), rank, world, [p.npts for p in allp])
+    probs = [allp[i] for i in idx]
     nsteps = probs[0].nsteps
     dev = torch.device("cuda", local)
     sizes = [p.npts for p in probs]
@@ -332,7 +334,7 @@ def run_sweep(args):
     total_ms, updates = D.reduce_step(total_ms, updates_local, dev)
     ms_per_step = total_ms / args.steps
     value = updates * args.steps / (total_ms * 1e-3)
-    hb = batch.hbar(u0s, us, nsteps)
+    hb = D.gather_rows(batch.hbar(u0s, us, nsteps), idx, len(allp), dev)   # every instance, in order
     cnt = batch.sync()
     groups = batch.groups()
 
@@ -391,7 +393,8 @@ def run_sweep(args):
                            "sizes": sorted(set(p.shape[0] for p in allp)), "h": 0.02, "W": "N/16",
                            "launch_groups": groups, "updates_per_step": updates, "autotune": tune,
                            "l2": "256 MiB buffer written between timed steps",
-                           "parallelism": "instances sharded over ranks" if world > 1 else "single GPU"},
+                           "parallelism": ("instances sharded over ranks by LPT on N^2, H-bar rows gathered"
+                                           if world > 1 else "single GPU")},
                 "per_instance_loop": loop,
                 "batched_vs_loop": (value / world / loop["value"]) if loop else None,
                 "hbar": {"mean": float(hb[:, 0].mean()), "min": float(hb[:, 0].min()),
