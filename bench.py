@@ -813,19 +813,21 @@ def run_ours(args):
     traffic = profile_traffic(args.workload, info["algo"], args.dtype)
     if info["algo"] == "brute":
         # brute force is bound by binary64 adds: one per window candidate per
-        # output and pass (+ the potential term); peak from the unit count:
-        # 2 binary64 adds per clock per SM (the nominal 1.25 TFLOP/s counts an
-        # FMA as two) x SMs x max SM clock
+        # output and pass (+ the potential term); peak: the device's add rate
+        # measured by the probe kernel (best of 3), next to the unit count's
+        # 2 binary64 adds per clock per SM x SMs x max SM clock
         import torch
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         clk_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-        peak_gops = 2.0 * sms * clk_mhz * 1e6 / 1e9
+        derived = 2.0 * sms * clk_mhz * 1e6 / 1e9
+        peak_gops = max(hjlo.probe_fp64_add(1 << 16) for _ in range(3)) / 1e9
         weffs = [info["dhi"][a] - info["dlo"][a] + 1 for a in range(p.ndim)]
         adds_launch = p.npts * (sum(weffs) + 1) / p.ndim
         ach = adds_launch / avg_launch_s / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": peak_gops, "unit": "G fp64 add/s",
                 "frac": ach / peak_gops, "traffic": None, "kernel": "hjlo::pass_kernel (brute)",
-                "peak_kind": "derived (2 adds/clk/SM x %d SMs x %.0f MHz)" % (sms, clk_mhz),
+                "peak_kind": "measured (hjlo_probe_fp64_add); derived 2 adds/clk/SM x %d SMs x %.0f MHz = %.0f"
+                             % (sms, clk_mhz, derived),
                 "fp64_adds_per_launch": adds_launch, "avg_launch_us": avg_launch_s * 1e6}
     else:
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
