@@ -68,6 +68,8 @@ def parse_args():
     ap.add_argument("--loop-instances", type=int, default=28,
                     help="sweep512: instances timed one plan at a time for the per-instance loop")
     ap.add_argument("--algo", choices=["monge", "brute", "auto"], default="monge")
+    ap.add_argument("--batch-mode", choices=["auto", "grouped", "persistent"], default="auto",
+                    help="sweep512: launch mode (auto: the faster on a 64-step trial)")
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -300,6 +302,30 @@ def run_sweep(args):
     batch = hjlo.Batch([(p.shape, p.dx, p.h, p.P, p.W) for p in probs], algo=algo)
     # every group's launch shapes from the library's autotuner (untimed)
     tune = None if args.no_autotune else batch.autotune(u0s, Vs, 8)
+    # launch mode: one launch per group and axis, or one persistent launch per
+    # time step; both timed on 64 steps (untimed for the bench), the faster kept
+    modes = {}
+    for mode in ("grouped", "persistent"):
+        try:
+            batch.set_persistent(mode == "persistent")
+        except hjlo.HjloError:
+            continue
+        ts = []
+        for _ in range(3):
+            u_all.copy_(u0_all)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(torch.cuda.current_stream())
+            batch.run(us, Vs, 64)
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        modes[mode] = min(ts[1:])
+    if args.batch_mode != "auto" and args.batch_mode in modes:
+        best_mode = args.batch_mode
+    else:
+        best_mode = min(modes, key=modes.get)
+    batch.set_persistent(best_mode == "persistent")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
@@ -379,7 +405,7 @@ def run_sweep(args):
                "sample": "sweep512 instances 0..%d, first 50 of %d steps each, %d OpenMP threads"
                          % (k - 1, nsteps, cores)}
 
-    launches = nsteps * 2 * groups
+    launches = nsteps if best_mode == "persistent" else nsteps * 2 * groups
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     alg_bytes_run = updates_local * 40.0            # 2D binary64: 2 passes x 16 B + h*V 8 B
@@ -392,6 +418,8 @@ def run_sweep(args):
                 "config": {"workload": "sweep512", "instances": len(allp), "nsteps": nsteps,
                            "sizes": sorted(set(p.shape[0] for p in allp)), "h": 0.02, "W": "N/16",
                            "launch_groups": groups, "updates_per_step": updates, "autotune": tune,
+                           "batch_mode": best_mode,
+                           "mode_trial_ms_per_64_steps": modes,
                            "l2": "256 MiB buffer written between timed steps",
                            "parallelism": ("instances sharded over ranks by LPT on N^2, H-bar rows gathered"
                                            if world > 1 else "single GPU")},
@@ -401,7 +429,8 @@ def run_sweep(args):
                          "max": float(hb[:, 0].max()), "first": [float(x) for x in hb[:4, 0]]},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": None,
-                             "kernel": "hjlo::pass_kernel_batch", "peak_kind": peak_kind,
+                             "kernel": ("hjlo::pass_kernel_persist" if best_mode == "persistent"
+                                        else "hjlo::pass_kernel_batch"), "peak_kind": peak_kind,
                              "alg_bytes_per_launch": alg_bytes_run / launches,
                              "avg_launch_us": avg_launch_s * 1e6},
                 "cpu_baseline": cpu, "clocks": clk,

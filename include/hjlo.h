@@ -337,6 +337,27 @@ hjlo_status hjlo_batch_autotune(hjlo_batch *batch, const void *const *u, const d
 /* Number of launch groups the batch formed (0 for NULL). */
 int32_t hjlo_batch_groups(const hjlo_batch *batch);
 
+/*
+ * How a batch's time steps are launched (no counterpart in the paper; the
+ * results are the same bit for bit either way).  on = 0: one kernel launch
+ * per launch group and axis, the groups as parallel branches of the
+ * captured graph.  on = 1: one persistent launch per time step over every
+ * instance and axis.  Its CTAs (as many as fit the GPU at once) take work
+ * items -- a few tiles of one instance's pass -- from a device queue that
+ * lists every axis-a item before any axis-(a+1) item; an item of axis a >= 1
+ * first waits until every tile of its instance's axis a - 1 pass is done (a
+ * per-instance tile counter), because that pass writes the grid this one
+ * reads.  Waits only point at items taken earlier by running CTAs, so the
+ * launch cannot deadlock; each wait is bounded (1 s), after which the
+ * launch raises the timeout flag that hjlo_batch_sync reports as
+ * HJLO_ETIMEOUT and skips the remaining waits.  The launch uses the largest
+ * thread count and shared memory of the groups' shapes.  Every instance must
+ * run the monotone search.  Waits for the batch's stream; the next
+ * hjlo_batch_run rebuilds the graph.  Errors: HJLO_EINVAL (NULL batch, on
+ * not 0 or 1), HJLO_EUNSUPPORTED (an instance runs brute force).
+ */
+hjlo_status hjlo_batch_set_persistent(hjlo_batch *batch, int32_t on);
+
 /* Wait for the plan's stream and copy its device counters into *out (host,
  * may be NULL).  Returns HJLO_EPRECOND / HJLO_ETIMEOUT if a launch since the
  * last call raised the corresponding flag (the flags are then cleared). */

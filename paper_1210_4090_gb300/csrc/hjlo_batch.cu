@@ -23,6 +23,25 @@
 
 using namespace hjlo;
 
+namespace hjlo {
+hjlo_status persist_occupancy_f64(int threads, size_t smem, int *blocks_per_sm);
+hjlo_status persist_occupancy_f32(int threads, size_t smem, int *blocks_per_sm);
+hjlo_status persist_launch_f64(const PersistParams &pp, int grid, int threads, size_t smem, cudaStream_t st);
+hjlo_status persist_launch_f32(const PersistParams &pp, int grid, int threads, size_t smem, cudaStream_t st);
+
+hjlo_status persist_occupancy(int dtype, int threads, size_t smem, int *blocks_per_sm)
+{
+    return dtype == HJLO_F64 ? persist_occupancy_f64(threads, smem, blocks_per_sm)
+                             : persist_occupancy_f32(threads, smem, blocks_per_sm);
+}
+
+hjlo_status persist_launch(int dtype, const PersistParams &pp, int grid, int threads, size_t smem, cudaStream_t st)
+{
+    return dtype == HJLO_F64 ? persist_launch_f64(pp, grid, threads, smem, st)
+                             : persist_launch_f32(pp, grid, threads, smem, st);
+}
+}  // namespace hjlo
+
 namespace {
 
 constexpr int kBatchGraphSteps = 8;
@@ -56,6 +75,21 @@ struct hjlo_batch {
     std::vector<const void *> graph_u;
     std::vector<const double *> graph_v;
     long long steps = 0;
+    // persistent mode (hjlo_batch_set_persistent): one launch per time step
+    int persist = 0;
+    bool pbuilt = false;                 // work list and shapes match the groups' current shapes
+    PersistItem *d_pwork = nullptr;
+    PassParams *d_pshapes = nullptr;
+    BatchItem *d_pitems = nullptr;       // [axis * count + instance]
+    int *d_ptiles = nullptr;             // [instance * ndim + axis]
+    unsigned long long *d_pstate = nullptr;   // the queue word, then done[count * ndim] (32-bit)
+    size_t pstate_bytes = 0;
+    std::vector<BatchItem> h_pitems;
+    long long pnwork = 0;
+    int pgrid = 0, pthreads = 0;
+    size_t psmem = 0;
+    long long pwait_ns = 1000000000LL;   // bound on a dependency wait (1 s)
+    int ptest_extra_dep = 0;             // test knob HJLO_TEST_EXTRA_DEP
 };
 
 namespace {
@@ -156,6 +190,11 @@ void release(hjlo_batch *b)
         if (g.done) cudaEventDestroy(g.done);
     }
     for (auto &ax : b->inst) cudaFree(ax.d_kr64);
+    cudaFree(b->d_pwork);
+    cudaFree(b->d_pshapes);
+    cudaFree(b->d_pitems);
+    cudaFree(b->d_ptiles);
+    cudaFree(b->d_pstate);
     cudaFree(b->d_counters);
     cudaFree(b->d_flags);
     cudaFree(b->d_hv);
@@ -191,6 +230,127 @@ void drop_graphs(hjlo_batch *b)
     if (b->graph_one) cudaGraphExecDestroy(b->graph_one);
     b->graph_many = nullptr;
     b->graph_one = nullptr;
+    b->pbuilt = false;                   // shapes may have changed
+}
+
+// The persistent launch's work list, launch shapes and state (device), from
+// the groups' current shapes.  Items of one axis come in groups of tiles of
+// one instance, largest instances first within an axis; an axis's items all
+// precede the next axis's, so every dependency wait points at items taken
+// earlier.  Chunks are sized for about 32 items per resident CTA.
+hjlo_status build_persist(hjlo_batch *b)
+{
+    const int nd = b->ndim, count = b->count;
+    const int ng = (int)b->groups.size();
+    std::vector<PassParams> shapes((size_t)ng * nd);
+    int threads = 32;
+    size_t smem = 0;
+    for (int gi = 0; gi < ng; ++gi)
+        for (int a = 0; a < nd; ++a) {
+            const AxisPlan &ax = b->groups[gi].ax[a];
+            if (ax.algo != KALGO_MONGE)
+                return set_error(HJLO_EUNSUPPORTED, "the persistent batch runs the monotone search only");
+            PassParams &pp = shapes[(size_t)gi * nd + a];
+            fill_params(ax, pp);
+            pp.counters = b->d_counters;
+            pp.flags = b->d_flags;
+            threads = std::max(threads, ax.threads);
+            smem = std::max(smem, ax.smem);
+        }
+    int per_sm = 0;
+    hjlo_status s = persist_occupancy(b->dtype, threads, smem, &per_sm);
+    if (s != HJLO_OK) return s;
+    if (per_sm < 1) return set_error(HJLO_EUNSUPPORTED, "the persistent batch's launch shape does not fit an SM");
+    DeviceFacts df;
+    if ((s = device_facts(df)) != HJLO_OK) return s;
+    const int grid = df.num_sms * per_sm;
+    std::vector<int> tiles((size_t)count * nd);
+    long long total = 0;
+    for (int gi = 0; gi < ng; ++gi)
+        for (int i : b->groups[gi].members)
+            for (int a = 0; a < nd; ++a) {
+                tiles[(size_t)i * nd + a] = (int)b->groups[gi].ax[a].ntiles;
+                total += b->groups[gi].ax[a].ntiles;
+            }
+    const long long chunk = std::max(1LL, total / (32LL * grid));
+    std::vector<PersistItem> work;
+    for (int a = 0; a < nd; ++a) {
+        std::vector<int> order(ng);
+        for (int gi = 0; gi < ng; ++gi) order[gi] = gi;
+        std::sort(order.begin(), order.end(), [&](int x, int y) {
+            const long long wx = b->groups[x].ax[a].ntiles * b->groups[x].ax[a].threads;
+            const long long wy = b->groups[y].ax[a].ntiles * b->groups[y].ax[a].threads;
+            return wx != wy ? wx > wy : x < y;
+        });
+        for (int gi : order) {
+            const Group &g = b->groups[gi];
+            const long long nt = g.ax[a].ntiles;
+            for (int i : g.members)
+                for (long long t = 0; t < nt; t += chunk) {
+                    PersistItem it;
+                    it.shape = gi * nd + a;
+                    it.inst = i;
+                    it.axis = a;
+                    it.tile0 = (int)t;
+                    it.ntile = (int)std::min(chunk, nt - t);
+                    it.pad = 0;
+                    work.push_back(it);
+                }
+        }
+    }
+    cudaFree(b->d_pwork);
+    cudaFree(b->d_pshapes);
+    cudaFree(b->d_ptiles);
+    b->d_pwork = nullptr;
+    b->d_pshapes = nullptr;
+    b->d_ptiles = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_pwork, sizeof(PersistItem) * work.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_pshapes, sizeof(PassParams) * shapes.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ptiles, sizeof(int) * tiles.size());
+    if (e == cudaSuccess && !b->d_pitems) e = cudaMalloc(&b->d_pitems, sizeof(BatchItem) * (size_t)count * nd);
+    if (e == cudaSuccess && !b->d_pstate) {
+        b->pstate_bytes = sizeof(unsigned long long) + sizeof(unsigned) * (size_t)count * nd;
+        e = cudaMalloc(&b->d_pstate, b->pstate_bytes);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pwork, work.data(), sizeof(PersistItem) * work.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pshapes, shapes.data(), sizeof(PassParams) * shapes.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_ptiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "persistent batch set-up");
+    b->pnwork = (long long)work.size();
+    b->pgrid = grid;
+    b->pthreads = threads;
+    b->psmem = smem;
+    const char *env = getenv("HJLO_TEST_EXTRA_DEP");
+    b->ptest_extra_dep = env ? std::max(0, atoi(env)) : 0;
+    env = getenv("HJLO_TEST_WAIT_NS");
+    b->pwait_ns = env ? std::max(0LL, atoll(env)) : 1000000000LL;
+    b->pbuilt = true;
+    return HJLO_OK;
+}
+
+// One time step of every instance in one persistent launch.
+hjlo_status enqueue_persist_step(hjlo_batch *b, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_pstate, 0, b->pstate_bytes, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(persistent state)");
+    PersistParams pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.work = b->d_pwork;
+    pp.nwork = b->pnwork;
+    pp.shapes = b->d_pshapes;
+    pp.items = b->d_pitems;
+    pp.tiles = b->d_ptiles;
+    pp.queue = b->d_pstate;
+    pp.done = reinterpret_cast<unsigned *>(b->d_pstate + 1);
+    pp.flags = b->d_flags;
+    pp.count = b->count;
+    pp.ndim = b->ndim;
+    pp.wait_ns = b->pwait_ns;
+    pp.test_extra_dep = b->ptest_extra_dep;
+    return persist_launch(b->dtype, pp, b->pgrid, b->pthreads, b->psmem, st);
 }
 
 // One step of every instance: each group on its own stream, forked from and
@@ -220,7 +380,12 @@ hjlo_status capture(hjlo_batch *b, int inner, cudaGraphExec_t *out)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
-    hjlo_status s = enqueue_batch_step(b, b->cap_stream, inner);
+    hjlo_status s = HJLO_OK;
+    if (b->persist) {
+        for (int k = 0; k < inner && s == HJLO_OK; ++k) s = enqueue_persist_step(b, b->cap_stream);
+    } else {
+        s = enqueue_batch_step(b, b->cap_stream, inner);
+    }
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (s != HJLO_OK) { if (g) cudaGraphDestroy(g); return s; }
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
@@ -406,6 +571,21 @@ hjlo_status hjlo_batch_run(hjlo_batch *b, void *const *u, const double *const *V
         }
     }
     hjlo_status s = HJLO_OK;
+    if (b->persist) {
+        if (!b->pbuilt) {
+            drop_graphs(b);
+            if ((s = build_persist(b)) != HJLO_OK) return s;
+        }
+        // the same per-instance fields, indexed by (axis, instance)
+        b->h_pitems.resize((size_t)b->count * b->ndim);
+        for (auto &g : b->groups)
+            for (int a = 0; a < b->ndim; ++a)
+                for (size_t m = 0; m < g.members.size(); ++m)
+                    b->h_pitems[(size_t)a * b->count + g.members[m]] = g.h_items[a][m];
+        e = cudaMemcpyAsync(b->d_pitems, b->h_pitems.data(), sizeof(BatchItem) * b->h_pitems.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(persistent items)");
+    }
     if (!b->graph_many) s = capture(b, kBatchGraphSteps, &b->graph_many);
     if (s == HJLO_OK && !b->graph_one) s = capture(b, 1, &b->graph_one);
     if (s != HJLO_OK) return s;
@@ -419,6 +599,25 @@ hjlo_status hjlo_batch_run(hjlo_batch *b, void *const *u, const double *const *V
         if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
     }
     b->steps += nsteps;
+    return HJLO_OK;
+}
+
+hjlo_status hjlo_batch_set_persistent(hjlo_batch *b, int32_t on)
+{
+    if (!b) return set_error(HJLO_EINVAL, "batch is NULL");
+    if (on != 0 && on != 1) return set_error(HJLO_EINVAL, "on must be 0 or 1");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    if (on)
+        for (auto &g : b->groups)
+            for (int a = 0; a < b->ndim; ++a)
+                if (g.ax[a].algo != KALGO_MONGE)
+                    return set_error(HJLO_EUNSUPPORTED, "the persistent batch runs the monotone search only");
+    if (on != b->persist) {
+        drop_graphs(b);
+        b->persist = on;
+    }
     return HJLO_OK;
 }
 

@@ -11,6 +11,7 @@
 
 #include "hjlo.h"
 #include "hjlo_device.cuh"
+#include "hjlo_persist.cuh"
 
 namespace hjlo {
 
@@ -95,6 +96,16 @@ std::vector<ShapeHints> tune_candidates(const AxisPlan &ax);
 // 3D TMA descriptor {inner, N, outer} of `ptr` for lines along a strided
 // axis; false if TMA cannot serve this pointer/shape.
 bool encode_strided(const AxisPlan &ax, int esize, const void *ptr, CUtensorMap *map);
+
+// The launch fields of one axis pass (the per-grid pointers left null).
+void fill_params(const AxisPlan &ax, PassParams &p);
+
+// The persistent batched pass (hjlo_persist_*.cu): shared-memory opt-in,
+// resident CTAs per SM for a launch shape, and the launch.
+hjlo_status persist_allow_smem_f64();
+hjlo_status persist_allow_smem_f32();
+hjlo_status persist_occupancy(int dtype, int threads, size_t smem, int *blocks_per_sm);
+hjlo_status persist_launch(int dtype, const PersistParams &pp, int grid, int threads, size_t smem, cudaStream_t st);
 
 // Enqueues one batched pass over `count` grids sharing ax's launch shape.
 hjlo_status launch_pass_batch(const AxisPlan &ax, int dtype, const BatchItem *d_items, long long count,

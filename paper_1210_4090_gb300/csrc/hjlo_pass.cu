@@ -502,6 +502,8 @@ hjlo_status prepare_kernels()
     if ((s = kern_allow_smem_f32_contig()) != HJLO_OK) return s;
     if ((s = kern_allow_smem_f32_strided()) != HJLO_OK) return s;
     if ((s = decomp_allow_smem()) != HJLO_OK) return s;
+    if ((s = persist_allow_smem_f64()) != HJLO_OK) return s;
+    if ((s = persist_allow_smem_f32()) != HJLO_OK) return s;
     encode_fn();
     if (dev < 64) done[dev] = true;
     return HJLO_OK;
@@ -526,7 +528,7 @@ static hjlo_status dispatch_batch(const AxisPlan &ax, int dtype, const BatchItem
     return strided ? kern_batch_f32_strided(ax, items, p, count, st) : kern_batch_f32_contig(ax, items, p, count, st);
 }
 
-static void fill_params(const AxisPlan &ax, PassParams &p)
+void fill_params(const AxisPlan &ax, PassParams &p)
 {
     memset(&p, 0, sizeof(p));
     p.kr64 = ax.d_kr64;

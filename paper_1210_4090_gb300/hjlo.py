@@ -85,6 +85,7 @@ _SIGS = [
     ("hjlo_plan_set_decomp", _i32, [_vp, _f64, _i32]),
     ("hjlo_probe_fp64_add", _i32, [_i64, _vp, _vp]),
     ("hjlo_noalloc_status", _i32, [_vp, _vp]),
+    ("hjlo_batch_set_persistent", _i32, [_vp, _i32]),
     ("hjlo_plan_autotune", _i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(TuneReport)]),
     ("hjlo_integral_create", _i32, [ctypes.POINTER(Desc), _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp,
                                     ctypes.POINTER(_vp)]),
@@ -403,6 +404,12 @@ class Batch:
                                  % (name, i, dtype, self.npts[i]))
             arr[i] = t.data_ptr()
         return arr
+
+    def set_persistent(self, on: bool = True):
+        """One persistent launch per time step over every instance and axis
+        (True) or one launch per group and axis (False); see
+        hjlo_batch_set_persistent.  Results are the same bit for bit."""
+        _check(lib().hjlo_batch_set_persistent(self._h, 1 if on else 0), "hjlo_batch_set_persistent")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
