@@ -263,13 +263,18 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
 // whole line does not fit in one CTA's shared memory or the axis has fewer
 // lines than half the SMs; they hold about one SM's share of the rows, at
 // least 2 (weff - 1) (a block stages vR + weff - 1 points for vR rows) and
-// at most what fits.  A hint (hinted > 0) replaces the share, within
-// [weff - 1, what fits].
+// at most what fits.  Brute force, whose rows cost weff candidates each
+// against one staged point, also takes blocks for wider windows (up to the
+// full torus window) on an axis with few lines, from one row per block: a
+// lone line then spreads over many SMs instead of one SM's binary64 pipe.
+// A hint (hinted > 0) replaces the share, within [weff - 1 (brute: 1), what
+// fits].
 static long long block_rows(const AxisPlan &ax, int esize, int algo, int num_sms, size_t smem_optin,
                             long long hinted)
 {
     const long long N = ax.N, w = ax.weff, lines = ax.outer;
-    if (ax.inner != 1 || 4 * w > N) return 0;
+    const bool brute = (algo == KALGO_BRUTE);
+    if (ax.inner != 1 || (4 * w > N && !brute)) return 0;
     // shared memory per staged point and per window entry (layout_smem)
     const long long per_pt = esize + 2 + ((algo == KALGO_MONGE) ? 4 : 0);
     const long long per_w = 8 + ((algo == KALGO_MONGE) ? 8 : 0);
@@ -277,11 +282,13 @@ static long long block_rows(const AxisPlan &ax, int esize, int algo, int num_sms
     const long long fit_pts = room > 0 ? room / per_pt : 0;         // staged points that fit
     const bool fits = N + w <= fit_pts;
     if (fits && 2 * lines >= num_sms) return 0;
-    long long vR = std::max(2 * (w - 1), (N * lines + num_sms - 1) / num_sms);
-    if (hinted > 0) vR = std::max(hinted, std::max(1LL, w - 1));
+    if (brute && 4 * w > N && !(2 * lines < num_sms)) return 0;     // wide windows: few lines only
+    const long long least = brute ? 1 : std::max(1LL, w - 1);
+    long long vR = std::max(brute ? 1 : 2 * (w - 1), (N * lines + num_sms - 1) / num_sms);
+    if (hinted > 0) vR = std::max(hinted, least);
     vR = std::min(vR, fit_pts - (w - 1));
     vR = std::min(vR, N - (w - 1));                                 // a block never spans the line
-    if (vR < std::max(1LL, w - 1) || vR >= N) return 0;
+    if (vR < least || vR >= N) return 0;
     return vR;
 }
 
@@ -393,7 +400,7 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
         // brute force: warps per line (rows interleaved) until the grid has
         // about 48 warps per SM, at least 4 rows per warp
         ax.wpl = 1;
-        while (ax.wpl < 16 && nlines * ax.wpl < 48LL * num_sms && 2LL * ax.wpl * 4 <= N &&
+        while (ax.wpl < 16 && nlines * ax.wpl < 48LL * num_sms && 2LL * ax.wpl * 4 <= NR &&
                32LL * 2 * ax.wpl * cmin <= 512)
             ax.wpl *= 2;
         ax.lpl = 32 * ax.wpl;
