@@ -629,13 +629,12 @@ def _time_run(plan, u0, V, nsteps, steps, warmup, tv=False):
 def run_decomp(args):
     """The paper's own fast convolution (Sec. 4, HJLO_ALGO_DECOMP) against the
     monotone pass on the same runs: the paper-size run (the pendulum of Sec.
-    5.1 on 2^18 points, T = 8; one line in row blocks) at eta = 0, where the
-    method is exact and the cut cannot change the result, and at the paper's
-    eta = dx with the approximate block-restart option (the whole 2^18-point
-    period does not fit one CTA, and at eta > 0 the method as the paper
-    defines it decomposes whole periods); the pendulum on 2 x 4096 points at
-    eta = 0, dx and 10 dx (the last two with block restarts, for the same
-    reason); the 1024^2 grid law for its first 100 steps at eta = 0 and dx
+    5.1 on 2^18 points, T = 8) at eta = 0 (exact: row blocks, the cut cannot
+    change the result), at the paper's eta = dx by the method as the paper
+    defines it (one decomposition per whole period, its cut spread over
+    CTAs) and at eta = dx with the approximate block-restart option; the
+    pendulum on 2 x 4096 points at eta = 0, dx and 10 dx (whole lines, one
+    CTA each); the 1024^2 grid law for its first 100 steps at eta = 0 and dx
     (whole lines).  Reports time, updates/s, components per line and pass,
     and the relative sup-norm deviation from the exact scheme (the monotone
     pass is bit-exact)."""
@@ -650,8 +649,8 @@ def run_decomp(args):
     big = WL.pendulum(2 ** 17)
     pend = WL.pendulum(4096)
     g = WL.grid1024(nsteps=100)
-    plan_cases = ((big, ((0.0, False), (big.dx[0], True))),
-                  (pend, ((0.0, False), (pend.dx[0], True), (10 * pend.dx[0], True))),
+    plan_cases = ((big, ((big.dx[0], False), (0.0, False), (big.dx[0], True))),
+                  (pend, ((0.0, False), (pend.dx[0], False), (10 * pend.dx[0], False))),
                   (g, ((0.0, False), (g.dx[0], False))))
     for p, etas in plan_cases:
         u0 = torch.tensor(p.u0, device=dev)
@@ -674,16 +673,17 @@ def run_decomp(args):
                           "eta": eta,
                           "method": ("block restarts (approximate)" if restart and eta > 0
                                      else "Sec. 4, one decomposition per period"),
-                          "row_blocks": info["row_blocks"], "decomp_ms": ms_d, "monge_ms": ms_m,
+                          "row_blocks": info["row_blocks"], "split_chunks": info["split_chunks"],
+                          "decomp_ms": ms_d, "monge_ms": ms_m,
                           "decomp_updates_per_s": p.npts * p.nsteps / (ms_d * 1e-3),
                           "monge_updates_per_s": p.npts * p.nsteps / (ms_m * 1e-3),
                           "components_per_line_pass": cnt["components"] / (runs * p.nsteps * lines_per_step),
                           "rel_error_vs_exact": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))})
-    # the line's value: the paper-size run (the pendulum with 2^18 points to
-    # T = 8) by the method as the paper defines it, at eta = 0 (exact); the
-    # paper timed its eta = dx variant at ~19 min, 262144 x 1634 updates /
-    # 1140 s (MATLAB, one 2.3 GHz laptop core: another machine and another
-    # tolerance, so the ratio is context)
+    # the line's value: the paper's timed run (the pendulum with 2^18 points
+    # to T = 8, tau = sqrt(dx), eta = dx) by the method as the paper defines
+    # it; the paper reports ~19 min for it, 262144 x 1634 updates / 1140 s
+    # (MATLAB, one 2.3 GHz laptop core: another machine, so the ratio is
+    # context)
     head = cases[0]
     paper = 262144 * 1634 / 1140.0
     line = {"metric": METRIC + " (decomposition method of Sec. 4)", "value": head["decomp_updates_per_s"],
@@ -691,8 +691,8 @@ def run_decomp(args):
             "ms_per_step": head["decomp_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["decomp_updates_per_s"] / paper, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "pendulum_2^18", "shape": head["shape"], "nsteps": head["nsteps"],
-                       "eta": 0.0, "W": head["W"],
-                       "baseline": "the paper's ~19 min (MATLAB, 2.3 GHz laptop core) for this run at eta = dx: "
+                       "eta_over_dx": 1.0, "W": head["W"], "split_chunks": head["split_chunks"],
+                       "baseline": "the paper's ~19 min (MATLAB, 2.3 GHz laptop core) for this run: "
                                    "%.3g updates/s" % paper,
                        "note": "comparison method; the headline path is the monotone pass"},
             "cases": cases}

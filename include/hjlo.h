@@ -104,6 +104,9 @@ typedef struct {
                                      the GPU; windows up to a quarter of the line) */
     int64_t block_rows[HJLO_MAX_DIM]; /* rows per block when row_blocks[a] > 1 (the last block
                                      holds the rest), else 0 */
+    int64_t split_chunks[HJLO_MAX_DIM]; /* HJLO_ALGO_DECOMP: 0, or the number of chunks each
+                                     line's period is cut into when its decomposition runs
+                                     whole across CTAs (see hjlo_plan_set_decomp) */
 } hjlo_plan_facts;
 
 /* Device-side counters of a plan (host struct filled by hjlo_sync). */
@@ -184,19 +187,23 @@ hjlo_status hjlo_plan_info(const hjlo_plan *plan, hjlo_plan_facts *info);
  * th:ccc), so the result does not depend on where the cut starts and long
  * or lonely contiguous lines run in row blocks, each cut on its own span.
  * At eta > 0 the result does depend on the cut: with restart_blocks = 0 each
- * line is decomposed whole (a line longer than one CTA holds, about 7000
- * points, is HJLO_EUNSUPPORTED); restart_blocks = 1 runs such lines in row
- * blocks that restart the decomposition at each block's first source, an
- * approximation of the method with no counterpart in the paper: every
- * output is still one candidate fl(u(y) + k(d)) of the scheme, so never
- * below it, and a component of m pieces treated as convex adds at most
- * eta dx_a m^2 to it (m <= block rows + window - 1).
+ * line is decomposed whole.  A line longer than one CTA holds (about 7000
+ * points) then has its period's cut and convolutions spread over many CTAs
+ * (chunks of the span cut locally and stitched into the one greedy cut of
+ * the whole period, then blocks of outputs; hjlo_plan_facts.split_chunks),
+ * with the same result as one CTA holding the whole line.  restart_blocks =
+ * 1 instead runs such lines in row blocks that restart the decomposition at
+ * each block's first source, an approximation of the method with no
+ * counterpart in the paper: every output is still one candidate
+ * fl(u(y) + k(d)) of the scheme, so never below it, and a component of m
+ * pieces treated as convex adds at most eta dx_a m^2 to it (m <= block rows
+ * + window - 1).
  *
  * Waits for the plan's stream; later steps use the new settings (the
  * plan's cached graph is rebuilt).  Errors: HJLO_EINVAL (another algorithm,
  * eta negative or not finite, restart_blocks not 0 or 1), HJLO_EUNSUPPORTED
- * (a line that does not fit whole at eta > 0 without restarts; the plan
- * keeps its previous settings).
+ * (a window too wide for the pass's shared memory), HJLO_ENOMEM; on error
+ * the plan keeps its previous settings.
  */
 hjlo_status hjlo_plan_set_decomp(hjlo_plan *plan, double eta, int32_t restart_blocks);
 

@@ -106,8 +106,10 @@ bool ranges_overlap(const void *a, const void *b, size_t n)
 // All passes of one step.  src -> dst for axis 0, then in place on dst.  An
 // axis in row blocks cannot run in place: a block stages its rows' window
 // span, which holds rows of other blocks, and a block that starts late would
-// read rows another block has already written.  Such a pass writes to the
-// plan's scratch and is copied back (stream-ordered, so graphs capture it).
+// read rows another block has already written (the same holds for the
+// write-back blocks of a decomposition cut across CTAs).  Such a pass writes
+// to the plan's scratch and is copied back (stream-ordered, so graphs
+// capture it).
 hjlo_status enqueue_step(hjlo_plan *p, const void *src, void *dst, const double *hv, double hv_scale,
                          int32_t *amin, cudaStream_t st)
 {
@@ -115,7 +117,7 @@ hjlo_status enqueue_step(hjlo_plan *p, const void *src, void *dst, const double 
     for (int a = 0; a < p->ndim; ++a) {
         const bool last = (a == p->ndim - 1);
         const void *from = (a == 0) ? src : dst;
-        const bool via_scratch = p->ax[a].vblocks > 1 && ranges_overlap(from, dst, bytes);
+        const bool via_scratch = (p->ax[a].vblocks > 1 || p->ax[a].dsplit) && ranges_overlap(from, dst, bytes);
         if (via_scratch && !p->d_scratch) return set_error(HJLO_ECUDA, "row-block scratch missing");
         hjlo_status s = launch_pass(p->ax[a], p->dtype, from, via_scratch ? p->d_scratch : dst, last ? hv : nullptr,
                                     last ? hv_scale : 0.0, amin ? amin + (long long)a * p->npts : nullptr,
@@ -141,7 +143,7 @@ hjlo_status enqueue_steps(hjlo_plan *p, void *u, const double *V, bool tv, long 
         for (int a = 0; a < p->ndim; ++a) {
             const bool last = (a == p->ndim - 1);
             void *next = cur;
-            if (p->ax[a].vblocks > 1) {
+            if (p->ax[a].vblocks > 1 || p->ax[a].dsplit) {
                 if (!p->d_scratch) return set_error(HJLO_ECUDA, "row-block scratch missing");
                 next = (cur == u) ? p->d_scratch : u;
             }
@@ -360,16 +362,21 @@ hjlo_status hjlo_plan_create(const hjlo_desc *d, void *cuda_stream, hjlo_plan **
         if (algo != KALGO_MONGE) all_monge = false;
         apply_test_knobs(ax);
         if (s == HJLO_OK) s = dmalloc((void **)&ax.d_kr64, sizeof(double) * ax.weff, "cudaMalloc(kernel table)");
+        if (s == HJLO_OK && ax.dsplit) {
+            ax.split_bytes = split_scratch_bytes(ax);
+            s = dmalloc(&ax.d_split, ax.split_bytes, "cudaMalloc(decomposition scratch)");
+        }
         if (s == HJLO_OK) {
             cudaError_t e = cudaMemcpy(ax.d_kr64, k64, sizeof(double) * ax.weff, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) s = cuda_error(e, "kernel table upload");
         }
+        if (s == HJLO_OK) s = split_prepare(ax, p->stream);
         free(k64);
         if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
     }
     p->algo = (d->algo == HJLO_ALGO_DECOMP) ? HJLO_ALGO_DECOMP : (all_monge ? HJLO_ALGO_MONGE : HJLO_ALGO_BRUTE);
     bool blocks = false;
-    for (int a = 0; a < p->ndim; ++a) blocks = blocks || p->ax[a].vblocks > 1;
+    for (int a = 0; a < p->ndim; ++a) blocks = blocks || p->ax[a].vblocks > 1 || p->ax[a].dsplit;
     s = blocks ? dmalloc(&p->d_scratch, (size_t)p->npts * p->esize, "cudaMalloc(row-block scratch)") : HJLO_OK;
     if (s != HJLO_OK) { hjlo_plan_destroy(p); return s; }
     s = dmalloc((void **)&p->d_counters, sizeof(unsigned long long) * CNT_N, "cudaMalloc(counters)");
@@ -391,6 +398,7 @@ hjlo_status hjlo_plan_destroy(hjlo_plan *p)
     destroy_graph(p);
     for (int a = 0; a < HJLO_MAX_DIM; ++a) {
         cudaFree(p->ax[a].d_kr64);
+        cudaFree(p->ax[a].d_split);
     }
     cudaFree(p->d_counters);
     cudaFree(p->d_flags);
@@ -426,6 +434,7 @@ hjlo_status hjlo_plan_info(const hjlo_plan *p, hjlo_plan_facts *info)
         info->curvature[a] = p->ax[a].curv;
         info->row_blocks[a] = p->ax[a].vblocks;
         info->block_rows[a] = (p->ax[a].vblocks > 1) ? p->ax[a].vR : 0;
+        info->split_chunks[a] = p->ax[a].dsplit ? p->ax[a].dB : 0;
     }
     return HJLO_OK;
 }
@@ -635,22 +644,42 @@ hjlo_status hjlo_plan_set_decomp(hjlo_plan *p, double eta, int32_t restart_block
     // whole unless the caller asked for restarts at each block
     const bool blocks_ok = (eta == 0.0) || restart_blocks;
     AxisPlan shaped[HJLO_MAX_DIM];
+    bool need_scratch = false;
     for (int a = 0; a < p->ndim; ++a) {
         shaped[a] = p->ax[a];
         if ((s = shape_decomp(shaped[a], df.smem_optin, df.num_sms, blocks_ok)) != HJLO_OK) return s;
-        if (shaped[a].vblocks > 1 && !p->d_scratch)
-            return set_error(HJLO_EUNSUPPORTED, "row blocks need the plan's scratch, which this plan has not");
+        need_scratch = need_scratch || shaped[a].vblocks > 1 || shaped[a].dsplit;
     }
+    // device memory the new shapes need, also before anything changes
+    void *fresh[HJLO_MAX_DIM] = {};
+    void *fresh_scratch = nullptr;
+    for (int a = 0; a < p->ndim && s == HJLO_OK; ++a)
+        if (split_scratch_bytes(shaped[a]) > p->ax[a].split_bytes)
+            s = dmalloc(&fresh[a], split_scratch_bytes(shaped[a]), "cudaMalloc(decomposition scratch)");
+    if (s == HJLO_OK && need_scratch && !p->d_scratch)
+        s = dmalloc(&fresh_scratch, (size_t)p->npts * p->esize, "cudaMalloc(row-block scratch)");
     // launches already enqueued keep their own copy of the parameters; the
     // cached graph holds the old value and is rebuilt on next use
-    cudaError_t e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    cudaError_t e = (s == HJLO_OK) ? cudaStreamSynchronize(p->stream) : cudaSuccess;
+    if (s != HJLO_OK || e != cudaSuccess) {
+        for (int a = 0; a < HJLO_MAX_DIM; ++a) cudaFree(fresh[a]);
+        cudaFree(fresh_scratch);
+        return (s != HJLO_OK) ? s : cuda_error(e, "cudaStreamSynchronize");
+    }
     // slopes per unit length (Sec. 4.1): the second differences along axis a
     // are compared with -eta * dx_a
     for (int a = 0; a < p->ndim; ++a) {
-        p->ax[a] = shaped[a];
+        p->ax[a] = shaped[a];             // keeps the axis's scratch pointer
+        if (fresh[a]) {
+            cudaFree(p->ax[a].d_split);
+            p->ax[a].d_split = fresh[a];
+            p->ax[a].split_bytes = split_scratch_bytes(shaped[a]);
+        }
         p->ax[a].eta = eta * p->desc.dx[a];
     }
+    if (fresh_scratch) p->d_scratch = fresh_scratch;
+    for (int a = 0; a < p->ndim; ++a)
+        if ((s = split_prepare(p->ax[a], p->stream)) != HJLO_OK) return s;
     p->decomp_restart = restart_blocks;
     destroy_graph(p);
     return HJLO_OK;

@@ -28,6 +28,7 @@
 // value is one candidate fl(u(y) + k(d)) of the scheme, so the pass is never
 // below the scheme's.
 #include "hjlo_internal.h"
+#include "hjlo_decomp.cuh"
 
 namespace hjlo {
 
@@ -93,23 +94,6 @@ __device__ int next_clear(const unsigned *bits, int from, int to, int none)
         if (++w > wlast) return none;
         word = ~bits[w];
     }
-}
-
-// Number of kernel slopes strictly below rho (the slopes increase).  The
-// slopes are held as order-preserving keys (kh, kl: dkey32's words, which
-// compare as the finite values do, -0 with +0), so the search uses 32-bit
-// integer compares and leaves the binary64 pipe to the candidates' adds.
-__device__ __forceinline__ int below(const unsigned *kh, const unsigned *kl, int n, double rho)
-{
-    unsigned h, l;
-    dkey32(rho, h, l);
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const unsigned a = kh[mid];
-        if (a < h || (a == h && kl[mid] < l)) lo = mid + 1; else hi = mid;
-    }
-    return lo;
 }
 
 // Number of entries of the non-decreasing F[0..m) that are <= i.
@@ -418,6 +402,7 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool bloc
     ax.vblocks = 1;
     ax.vR = 0;
     ax.vNp = 0;
+    ax.dsplit = 0;
     if (ax.weff >= 3 && !(ax.curv > 0))
         return set_error(HJLO_EPRECOND, "the decomposition pass needs a strictly convex kernel table");
     // Row blocks for a contiguous axis (blocks_ok), as for the other passes:
@@ -443,13 +428,15 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool bloc
     }
     const long long rowsN = (ax.vblocks > 1) ? ax.vR : N;
     ax.smem = decomp_smem(ax, rowsN, nullptr);
+    // a line decomposed whole that does not fit one CTA: the period's cut and
+    // convolutions across CTAs (hjlo_split.cu); HJLO_DECOMP_SPLIT=1 takes
+    // that path for every line (tests)
+    const char *force = getenv("HJLO_DECOMP_SPLIT");
+    if ((force && atoi(force) == 1) ||
+        (!blocks_ok && (ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))))
+        return shape_split(ax, smem_optin, num_sms);
     if (ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))
-        return set_error(HJLO_EUNSUPPORTED,
-                         blocks_ok ? "a line of %lld points does not fit the decomposition pass"
-                                   : "a line of %lld points does not fit one CTA: with eta > 0 the decomposition of a "
-                                     "period needs the whole line (hjlo_plan_set_decomp's restart option runs it in "
-                                     "row blocks, approximately)",
-                         ax.N);
+        return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit the decomposition pass", ax.N);
     ax.ntiles = ax.inner * ax.outer * ax.vblocks;
     // one CTA per line: few lines (a 1D problem) get 32 warps each to hide
     // the latency of their components' searches; many lines get 8 warps

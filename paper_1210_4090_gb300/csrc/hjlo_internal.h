@@ -31,6 +31,13 @@ struct AxisPlan {
     int test_extra_tx = 0;                 // test knob, see apply_test_knobs
     int wide_mul = 2, wide_add = 8;        // warp offload of wide brackets (see PassParams)
     double eta = 0.0;                      // DECOMP: convexity tolerance of the decomposition
+    // DECOMP with a period cut across CTAs (dsplit = 1): chunks of dchunk
+    // points (dB per line) for the cut, write-back blocks of dvR outputs
+    // (dnblk per line), the passes' device scratch (owned by the plan)
+    int dsplit = 0, dchunk = 0, dB = 0, dvR = 0;
+    long long dnblk = 0;
+    void *d_split = nullptr;
+    size_t split_bytes = 0;
     // row blocks of a contiguous axis (vblocks > 1): each line is cut into
     // vblocks blocks of vR rows, each launched as a line of vNp = vR + weff - 1
     // points (see PassParams); the launch fields below then describe those
@@ -148,6 +155,15 @@ hjlo_status kern_batch_f32_strided(const AxisPlan &ax, const BatchItem *items, c
 
 // The paper's decomposition method as an axis pass (hjlo_decomp.cu).
 hjlo_status decomp_allow_smem();
+// The decomposition pass over whole periods cut across CTAs (hjlo_split.cu):
+// launch shape and scratch size of an axis, its scratch, its launches.
+hjlo_status shape_split(AxisPlan &ax, size_t smem_optin, int num_sms);
+size_t split_scratch_bytes(const AxisPlan &ax);
+hjlo_status split_allow_smem();
+// Per-plan set-up of an axis's scratch (the kernel's slope keys), after it is allocated.
+hjlo_status split_prepare(const AxisPlan &ax, cudaStream_t st);
+hjlo_status launch_split(const AxisPlan &ax, const void *src, void *dst, const double *hv, double hv_scale,
+                         unsigned long long *counters, int *flags, cudaStream_t st);
 // blocks_ok: a contiguous axis may run in row blocks (each decomposed on its
 // own span); false: whole lines only (EUNSUPPORTED when a line does not fit).
 hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool blocks_ok = true);

@@ -509,6 +509,7 @@ hjlo_status prepare_kernels()
     if ((s = kern_allow_smem_f32_contig()) != HJLO_OK) return s;
     if ((s = kern_allow_smem_f32_strided()) != HJLO_OK) return s;
     if ((s = decomp_allow_smem()) != HJLO_OK) return s;
+    if ((s = split_allow_smem()) != HJLO_OK) return s;
     if ((s = persist_allow_smem_f64()) != HJLO_OK) return s;
     if ((s = persist_allow_smem_f32()) != HJLO_OK) return s;
     encode_fn();
@@ -619,7 +620,8 @@ hjlo_status launch_pass(const AxisPlan &ax, int dtype, const void *src, void *ds
     if (ax.algo == KALGO_DECOMP) {
         if (amin) return set_error(HJLO_EUNSUPPORTED, "the decomposition method records no argmins");
         if (dtype != HJLO_F64) return set_error(HJLO_EUNSUPPORTED, "the decomposition method runs in binary64");
-        return launch_decomp(ax, src, dst, hv, hv_scale, counters, flags, st);
+        return ax.dsplit ? launch_split(ax, src, dst, hv, hv_scale, counters, flags, st)
+                         : launch_decomp(ax, src, dst, hv, hv_scale, counters, flags, st);
     }
     const int esize = (dtype == HJLO_F64) ? 8 : 4;
     PassParams p;

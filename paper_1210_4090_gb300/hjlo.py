@@ -38,7 +38,7 @@ class Desc(ctypes.Structure):
 class Facts(ctypes.Structure):
     _fields_ = [("ndim", _i32), ("algo", _i32), ("dlo", _i64 * 3), ("dhi", _i64 * 3),
                 ("centre", _i64 * 3), ("kmin", _f64 * 3), ("curvature", _f64 * 3), ("npts", _i64),
-                ("row_blocks", _i64 * 3), ("block_rows", _i64 * 3)]
+                ("row_blocks", _i64 * 3), ("block_rows", _i64 * 3), ("split_chunks", _i64 * 3)]
 
 
 class Counters(ctypes.Structure):
@@ -293,7 +293,8 @@ class Plan:
         return {"algo": {1: "brute", 2: "monge", 3: "decomp"}.get(f.algo, f.algo), "npts": f.npts,
                 "dlo": list(f.dlo[:nd]), "dhi": list(f.dhi[:nd]), "centre": list(f.centre[:nd]),
                 "kmin": list(f.kmin[:nd]), "curvature": list(f.curvature[:nd]),
-                "row_blocks": list(f.row_blocks[:nd]), "block_rows": list(f.block_rows[:nd])}
+                "row_blocks": list(f.row_blocks[:nd]), "block_rows": list(f.block_rows[:nd]),
+                "split_chunks": list(f.split_chunks[:nd])}
 
     def step(self, u_in, u_out=None, V=None, argmin=None):
         """One step; returns u_out (u_in itself when u_out is None: in place)."""

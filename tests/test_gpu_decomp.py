@@ -158,17 +158,18 @@ def test_row_blocks_at_zero_tolerance():
     assert np.array_equal(got.view(np.int64), O.run(u0, 1.0 / N, h, P, W, V, n).view(np.int64))
 
 
-def test_whole_line_needed_at_positive_tolerance():
+def test_whole_line_at_positive_tolerance():
     """At eta > 0 a period is decomposed whole: a line longer than one CTA
-    holds is refused unless the caller asks for block restarts."""
+    holds has its cut spread over CTAs (hjlo_split.cu) unless the caller asks
+    for block restarts, which run it in row blocks."""
     H = _hjlo()
     N, W, h, P, u0, V = _long_line()
     plan = H.Plan((N,), 1.0 / N, h, P, W, algo=H.ALGO_DECOMP)
-    with pytest.raises(H.HjloError) as e:
-        plan.set_tolerance(1.0)
-    assert e.value.status == 6
+    assert plan.info()["row_blocks"][0] > 1 and plan.info()["split_chunks"][0] == 0
+    plan.set_tolerance(1.0)
+    assert plan.info()["row_blocks"][0] == 1 and plan.info()["split_chunks"][0] > 1
     plan.set_tolerance(1.0, restart_blocks=True)
-    assert plan.info()["row_blocks"][0] > 1
+    assert plan.info()["row_blocks"][0] > 1 and plan.info()["split_chunks"][0] == 0
     plan.close()
 
 
