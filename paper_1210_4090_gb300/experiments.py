@@ -17,7 +17,7 @@ import numpy as np
 
 from . import workloads as WL
 
-__all__ = ["solve_gpu", "restrict", "relative_error", "convergence", "LAWS"]
+__all__ = ["solve_gpu", "solve_decomp_gpu", "restrict", "relative_error", "convergence", "LAWS"]
 
 LAWS = {"pendulum": WL.pendulum, "tdep": WL.tdep}
 
@@ -38,6 +38,34 @@ def solve_gpu(p: WL.Problem) -> np.ndarray:
         if cnt["error_flags"]:
             raise RuntimeError("device error flags %d" % cnt["error_flags"])
         return u.cpu().numpy()
+    finally:
+        plan.close()
+
+
+def solve_decomp_gpu(p: WL.Problem, eta: float = 0.0, nsteps: int | None = None, restart_blocks: bool = False):
+    """u after nsteps (default: to the problem's final time) by the paper's
+    own method (Sec. 4, HJLO_ALGO_DECOMP) at tolerance eta on the slopes
+    (per unit length, as Sec. 4.1 takes them; the paper's timed run uses
+    eta = dx), and the components per line and pass.  Each period is
+    decomposed whole unless restart_blocks asks for the row-block
+    approximation."""
+    import torch
+    from . import hjlo
+    n = p.nsteps if nsteps is None else int(nsteps)
+    plan = hjlo.Plan(p.shape, p.dx, p.h, p.P, p.W, algo=hjlo.ALGO_DECOMP)
+    try:
+        plan.set_tolerance(float(eta), restart_blocks=restart_blocks)
+        u = torch.tensor(p.u0, dtype=torch.float64, device="cuda")
+        V = None if p.V is None else torch.tensor(p.V, dtype=torch.float64, device="cuda")
+        if p.V_per_step:
+            plan.run_tv(u, V, n)
+        else:
+            plan.run(u, V, n)
+        cnt = plan.sync()
+        if cnt["error_flags"]:
+            raise RuntimeError("device error flags %d" % cnt["error_flags"])
+        lines = sum(int(np.prod(p.shape)) // s for s in p.shape)
+        return u.cpu().numpy(), cnt["components"] / max(1, n * lines)
     finally:
         plan.close()
 

@@ -114,7 +114,7 @@ def _long_line():
     return N, W, h, P, u0, V
 
 
-@pytest.mark.parametrize("eta", [1.0, 10.0])
+@pytest.mark.parametrize("eta", [1.0 / 12000, 1.0, 10.0])
 def test_long_line_whole_period(eta):
     """A line longer than one CTA holds, at eta > 0, without restarts: its
     period is cut across CTAs, with the oracle's components and values."""
@@ -133,9 +133,10 @@ def test_paper_pendulum_whole_period():
     periods, bit for bit the oracle's."""
     p = WL.pendulum(K=8192)
     n = 3
-    got, cnt, info = gpu_decomp(p.shape, p.dx, p.h, p.P, p.W, p.u0, p.V, n, 1.0)
+    eta = p.dx[0]
+    got, cnt, info = gpu_decomp(p.shape, p.dx, p.h, p.P, p.W, p.u0, p.V, n, eta)
     assert info["split_chunks"][0] > 1 and cnt["error_flags"] == 0
-    ref, ncomp = O.decomp_run(p.u0, p.dx, p.h, p.P, p.W, p.V, n, 1.0)
+    ref, ncomp = O.decomp_run(p.u0, p.dx, p.h, p.P, p.W, p.V, n, eta)
     assert np.array_equal(_bits(got), _bits(ref))
     assert cnt["components"] == ncomp
 
@@ -153,9 +154,9 @@ def test_paper_size_run_first_step(monkeypatch):
     dlo, dhi, k = O.table(N, dx, p.h, p.P[0], p.W[0])
     n = dhi - dlo
     src = p.u0[(np.arange(N + n) - dhi) % N]
-    got, cnt, info = gpu_decomp(p.shape, p.dx, p.h, p.P, p.W, p.u0, None, 1, 1.0)
+    got, cnt, info = gpu_decomp(p.shape, p.dx, p.h, p.P, p.W, p.u0, None, 1, dx)
     assert info["split_chunks"][0] > 1 and cnt["error_flags"] == 0
-    assert cnt["components"] == len(O.decompose(src, 1.0 * dx))
+    assert cnt["components"] == len(O.decompose(src, dx * dx))      # second differences >= -eta dx
     exact = O.run(p.u0, p.dx, p.h, p.P, p.W, None, 1)
     assert np.all(got >= exact)
     hit = np.zeros(N, dtype=bool)
@@ -166,3 +167,17 @@ def test_paper_size_run_first_step(monkeypatch):
     exact2, _, info2 = gpu_decomp(p.shape, p.dx, p.h, p.P, p.W, p.u0, p.V, 2, 0.0)
     assert info2["split_chunks"][0] > 1
     assert np.array_equal(_bits(exact2), _bits(O.run(p.u0, p.dx, p.h, p.P, p.W, p.V, 2)))
+
+
+def test_whole_run_through_the_experiment_helper(monkeypatch):
+    """The paper's pendulum on 2 x 256 points to T = 8 (73 steps) by the
+    method at eta = dx, every pass on the split path: bit for bit the
+    oracle's run, shocks and all."""
+    from paper_1210_4090_gb300 import experiments as E
+    monkeypatch.setenv("HJLO_DECOMP_SPLIT", "1")
+    monkeypatch.setenv("HJLO_DECOMP_CHUNK", "128")
+    p = WL.pendulum(256)
+    got, comps = E.solve_decomp_gpu(p, p.dx[0])
+    ref, ncomp = O.decomp_run(p.u0, p.dx, p.h, p.P, p.W, p.V, p.nsteps, p.dx[0])
+    assert np.array_equal(_bits(got), _bits(ref))
+    assert comps == ncomp / p.nsteps
