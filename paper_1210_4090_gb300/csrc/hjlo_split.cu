@@ -48,7 +48,7 @@ constexpr int kStitchThreads = 1024;
 constexpr int kCutWarps = 4;                 // chunks per CTA in the local cut (a warp each)
 constexpr int kMaxChunkWords = 128;          // chunks of at most 4096 points
 constexpr int kDefaultChunk = 1024;
-constexpr size_t kStitchStage = 160 * 1024;  // local starts and exits staged for the walk up to this size
+constexpr size_t kStitchStage = 200 * 1024;  // the stitch walk's data staged in shared memory up to this size
 
 struct SplitParams {
     const double *src;
@@ -381,7 +381,8 @@ __device__ Run block_scan_run(Run v, Run *wt, Run *total)
 }
 
 // One CTA per line.  Warp 0 walks the true cut from point 0, on the local
-// starts and exits staged in shared memory when they fit (stage_words > 0);
+// starts, rule bitmaps and chunk summaries staged in shared memory when they
+// fit (stage = 1; lines up to about 2^19 points);
 // then the CTA scans the chain's state at every chunk's first piece.  The
 // chunks mark their true starts themselves (split_pieces).
 __global__ void __launch_bounds__(kStitchThreads) split_stitch(SplitParams p, int stage)
@@ -402,14 +403,28 @@ __global__ void __launch_bounds__(kStitchThreads) split_stitch(SplitParams p, in
     int *cs = p.cs + line * B, *cm = p.cm + line * B;
     const int *F = p.F + line * p.Pl;
     if (stage) {
-        unsigned *sts = reinterpret_cast<unsigned *>(smem);
-        int *sx = reinterpret_cast<int *>(smem + sizeof(unsigned) * p.Wl);
-#pragma unroll 8
-        for (long long i = tid; i < p.Wl; i += blockDim.x) sts[i] = ts[i];
+        // the walk's reads, all of them, from shared memory: local starts,
+        // both rule bitmaps, the chunks' exits and first failing points
+        unsigned *sts = reinterpret_cast<unsigned *>(smem), *scv = sts + p.Wl, *scc = scv + p.Wl;
+        int *sx = reinterpret_cast<int *>(scc + p.Wl), *sfv = sx + B, *sfc = sfv + B;
 #pragma unroll 4
-        for (int i = tid; i < B; i += blockDim.x) sx[i] = X[i];
+        for (long long i = tid; i < p.Wl; i += blockDim.x) {
+            sts[i] = ts[i];
+            scv[i] = cv[i];
+            scc[i] = cc[i];
+        }
+#pragma unroll 2
+        for (int i = tid; i < B; i += blockDim.x) {
+            sx[i] = X[i];
+            sfv[i] = fcv[i];
+            sfc[i] = fcc[i];
+        }
         ts = sts;
+        cv = scv;
+        cc = scc;
         X = sx;
+        fcv = sfv;
+        fcc = sfc;
         __syncthreads();
     }
     if (warp == 0) {
@@ -917,7 +932,7 @@ hjlo_status launch_split(const AxisPlan &ax, const void *src, void *dst, const d
     const long long chunks = p.lines * p.B;
     split_classify<<<(unsigned)chunks, kSplitThreads, 0, st>>>(p);
     split_local_cut<<<(unsigned)((chunks + kCutWarps - 1) / kCutWarps), 32 * kCutWarps, 0, st>>>(p);
-    const size_t stage = sizeof(int) * (size_t)(p.Wl + p.B);
+    const size_t stage = sizeof(int) * 3 * (size_t)(p.Wl + p.B);
     const bool staged = stage <= kStitchStage;
     split_stitch<<<(unsigned)p.lines, kStitchThreads, staged ? stage : 0, st>>>(p, staged ? 1 : 0);
     split_pieces<<<(unsigned)chunks, kSplitThreads, 0, st>>>(p);
