@@ -152,7 +152,8 @@ typedef struct {
  * (HJLO_EPRECOND otherwise) and records no argmins (hjlo_step with
  * argmin_out and hjlo_adjoint return HJLO_EUNSUPPORTED).
  * Errors: HJLO_EINVAL (bad descriptor), HJLO_EUNSUPPORTED (a line of the grid
- * does not fit in one CTA's shared memory and cannot run in row blocks),
+ * does not fit in one CTA's shared memory and cannot run in row blocks or,
+ * for HJLO_ALGO_DECOMP, with its period spread across CTAs),
  * HJLO_EPRECOND, HJLO_ENOMEM, HJLO_ECUDA.
  */
 hjlo_status hjlo_plan_create(const hjlo_desc *desc, void *cuda_stream, hjlo_plan **out);
@@ -458,6 +459,10 @@ typedef struct {
     int64_t row_blocks;           /* 1: whole lines; k > 1: every line cut into k blocks of rows */
     int64_t block_rows;           /* rows per block (the last holds the rest); 0 for whole lines */
     int64_t line_points;          /* points staged per launched line: N, or block_rows + weff - 1 */
+    int64_t split_chunks;         /* HJLO_ALGO_DECOMP: 0, or the chunks of each line's period when its
+                                     decomposition runs across CTAs; tiles then counts the CTAs of the
+                                     write-back launch */
+    int64_t split_rows;           /* outputs per write-back CTA of that launch (0 otherwise) */
 } hjlo_shape_info;
 
 /*

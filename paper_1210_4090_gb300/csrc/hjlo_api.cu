@@ -282,6 +282,8 @@ hjlo_status hjlo_shape_query(int64_t N, int64_t lines, int64_t weff, int32_t esi
         out->row_blocks = ax.vblocks;
         out->block_rows = blocks ? ax.vR : 0;
         out->line_points = blocks ? ax.vR + weff - 1 : N;
+        out->split_chunks = ax.dsplit ? ax.dB : 0;
+        out->split_rows = ax.dsplit ? ax.dvR : 0;
         return HJLO_OK;
     }
     hjlo_status s = shape_launch(ax, esize, algo == HJLO_ALGO_BRUTE ? KALGO_BRUTE : KALGO_MONGE, num_sms,

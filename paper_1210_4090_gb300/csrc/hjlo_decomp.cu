@@ -428,12 +428,12 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool bloc
     }
     const long long rowsN = (ax.vblocks > 1) ? ax.vR : N;
     ax.smem = decomp_smem(ax, rowsN, nullptr);
-    // a line decomposed whole that does not fit one CTA: the period's cut and
+    // a line that fits neither one CTA nor row blocks (eta > 0 without
+    // restarts, a strided axis, a wide window): the period's cut and
     // convolutions across CTAs (hjlo_split.cu); HJLO_DECOMP_SPLIT=1 takes
     // that path for every line (tests)
     const char *force = getenv("HJLO_DECOMP_SPLIT");
-    if ((force && atoi(force) == 1) ||
-        (!blocks_ok && (ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))))
+    if ((force && atoi(force) == 1) || ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))
         return shape_split(ax, smem_optin, num_sms);
     if (ax.smem > smem_optin || rowsN + ax.weff > (1LL << 30))
         return set_error(HJLO_EUNSUPPORTED, "a line of %lld points does not fit the decomposition pass", ax.N);

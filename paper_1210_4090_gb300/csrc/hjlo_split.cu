@@ -824,7 +824,7 @@ hjlo_status shape_split(AxisPlan &ax, size_t smem_optin, int num_sms)
     ax.dvR = (int)vR;
     ax.dnblk = nblk;
     ax.smem = emit_smem((int)vR, (int)n);
-    ax.threads = kSplitThreads;
+    ax.threads = kEmitThreads;                 // the write-back launch, which ntiles counts
     ax.ntiles = lines * nblk;
     ax.C = 1;
     ax.log2C = 0;

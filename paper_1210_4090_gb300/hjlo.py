@@ -71,7 +71,7 @@ _lib = None
 class ShapeInfo(ctypes.Structure):
     _fields_ = [("lanes_per_line", _i32), ("segment_rows", _i32), ("lines_per_tile", _i32), ("threads", _i32),
                 ("smem_bytes", _i64), ("tiles", _i64), ("row_blocks", _i64), ("block_rows", _i64),
-                ("line_points", _i64)]
+                ("line_points", _i64), ("split_chunks", _i64), ("split_rows", _i64)]
 
 
 _SIGS = [

@@ -127,6 +127,33 @@ def test_long_line_whole_period(eta):
     assert cnt["components"] == ncomp
 
 
+@pytest.mark.parametrize("eta", [0.0, 0.5])
+@pytest.mark.parametrize("shape", [(2, 12000), (12000, 3)], ids=["contiguous", "strided"])
+def test_long_lines_in_2d(shape, eta):
+    """Long lines on a 2D grid: two contiguous lines (row blocks at eta = 0,
+    whole periods across CTAs at eta > 0), and a strided long axis, which
+    row blocks cannot serve, across CTAs at every tolerance."""
+    rng = np.random.default_rng(sum(shape))
+    dx = tuple(1.0 / s for s in shape)
+    W = tuple(min(30, s // 3) for s in shape)
+    P = (0.2, -0.3)
+    u0 = np.cumsum(rng.normal(size=shape), axis=-1) * 0.01 + np.cumsum(rng.normal(size=shape), axis=0) * 0.01
+    V = rng.normal(size=shape) * 0.1
+    got, cnt, info = gpu_decomp(shape, dx, 2e-3, P, W, u0, V, 2, eta)
+    long_axis = int(np.argmax(shape))
+    if long_axis == 1 and eta == 0.0:
+        assert info["row_blocks"][1] > 1 and info["split_chunks"][1] == 0
+    else:
+        assert info["split_chunks"][long_axis] > 1
+    assert cnt["error_flags"] == 0
+    ref, ncomp = O.decomp_run(u0, dx, 2e-3, P, W, V, 2, eta)
+    assert np.array_equal(_bits(got), _bits(ref))
+    if max(info["row_blocks"]) == 1:               # row blocks cut each block's span on its own
+        assert cnt["components"] == ncomp
+    if eta == 0.0:
+        assert np.array_equal(_bits(got), _bits(O.run(u0, dx, 2e-3, P, W, V, 2)))
+
+
 def test_paper_pendulum_whole_period():
     """The paper's pendulum (Sec. 5.1) on 2 x 8192 points at eta = dx, the
     tolerance of its timed run: the first steps by the method on whole

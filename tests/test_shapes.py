@@ -81,9 +81,10 @@ def test_decomposition_shape_invariants(num_sms, smem):
     """The decomposition pass: one CTA per line or row block, shared memory
     within the CTA's, and for row blocks the blocks cover the line and a
     block's span of sources (its rows + weff - 1) is no longer than the line,
-    as its gather (one wrap at most) needs."""
+    as its gather (one wrap at most) needs; a line that fits neither runs
+    across CTAs, its write-back blocks covering the line."""
     from paper_1210_4090_gb300 import hjlo
-    ok = 0
+    ok = split = 0
     for N, lines, weff in _cases():
         try:
             s = hjlo.shape_query(N, lines, weff, 8, 3, num_sms, smem)
@@ -94,6 +95,16 @@ def test_decomposition_shape_invariants(num_sms, smem):
         case = (N, lines, weff, s)
         assert s["threads"] in (256, 1024) and 0 < s["smem_bytes"] <= smem, case
         blocks, R, L = s["row_blocks"], s["block_rows"], s["line_points"]
+        if s["split_chunks"]:
+            # a line that fits neither one CTA nor row blocks: its period cut
+            # into chunks across CTAs, the outputs in blocks of split_rows
+            split += 1
+            V = s["split_rows"]
+            assert blocks == 1 and R == 0 and 1 <= V <= N, case
+            assert s["split_chunks"] * 4096 >= N + weff - 1 > (s["split_chunks"] - 1) * 64, case
+            assert s["tiles"] == lines * -(-N // V), case
+            continue
+        assert s["split_rows"] == 0, case
         assert s["tiles"] == lines * blocks, case
         if blocks > 1:
             assert 4 * weff <= N and R >= max(1, weff - 1), case
@@ -101,7 +112,7 @@ def test_decomposition_shape_invariants(num_sms, smem):
             assert L == R + weff - 1 <= N, case
         else:
             assert R == 0 and L == N, case
-    assert ok > 50
+    assert ok > 50 and split >= 1
 
 
 def test_shape_query_rejects_bad_arguments():
