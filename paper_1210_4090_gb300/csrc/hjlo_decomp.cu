@@ -42,6 +42,7 @@ constexpr int kLongComponent = 512;    // components of at least this many piece
 constexpr int kMaxLong = 64;           // listed long components per CTA (the rest stay with a warp)
 constexpr int kMiscWarpTotals = 4;     // misc[4..36): warp totals of a block scan
 constexpr int kMiscLongList = 36;      // misc[36..36+kMaxLong): indices of the long components
+constexpr long long kSplitMinPoints = 4096;   // shorter lonely lines stay in one CTA (one launch, not five)
 
 struct DecompParams {
     const double *src;
@@ -415,6 +416,11 @@ hjlo_status shape_decomp(AxisPlan &ax, size_t smem_optin, int num_sms, bool bloc
     // of 3272).
     const long long N = ax.N, w = ax.weff, lines = ax.outer;
     const bool fits = decomp_smem(ax, N, nullptr) <= smem_optin;
+    // whole periods (eta > 0) of a few long lines would leave most SMs idle
+    // with one CTA per line: spread each period across CTAs instead (the
+    // 2 x 4096-point pendulum at eta = dx, 289 steps: 7.7 ms against 14.7)
+    if (!blocks_ok && N >= kSplitMinPoints && 2 * lines * ax.inner < num_sms)
+        return shape_split(ax, smem_optin, num_sms);
     if (blocks_ok && ax.inner == 1 && 4 * w <= N && (!fits || 2 * lines < num_sms)) {
         long long vR = std::max(std::max(1LL, w - 1), (N * lines + num_sms - 1) / num_sms);
         const ShapeHints hint = env_hints();
