@@ -445,6 +445,7 @@ hjlo_status hjlo_batch_create(const hjlo_desc *descs, int32_t count, void *cuda_
             ax.outer = outer;
             double *k64 = nullptr;
             s = resolve_axis(d.shape[a], d.dx[a], d.h, d.P[a], d.window[a], ax, &k64);
+            ax.t8_ok = 0;                     // the batched kernels keep 16-bit argmin offsets
             if (s != HJLO_OK) break;
             int algo = KALGO_MONGE;
             if (d.algo == HJLO_ALGO_BRUTE) algo = KALGO_BRUTE;

@@ -384,12 +384,25 @@ __device__ __forceinline__ int screened_row(const PassParams &p, const T *su, co
                                             int &rescans)
 {
     int m1 = 0x7fffffff, m2 = 0x7fffffff, t1 = tlo;
+    if (thi - tlo < 4) {
+        // short brackets (most rows of the divide and conquer): four
+        // candidates without a loop, those past thi masked
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = min(tlo + q, thi);
+            const int c = (tlo + q <= thi) ? f[t] + k[t] : 0x7fffffff;
+            m2 = min(m2, max(m1, c));
+            t1 = (c < m1) ? t : t1;
+            m1 = min(m1, c);
+        }
+    } else {
 #pragma unroll 4
-    for (int t = tlo; t <= thi; ++t) {
-        int c = f[t] + k[t];
-        m2 = min(m2, max(m1, c));
-        t1 = (c < m1) ? t : t1;
-        m1 = min(m1, c);
+        for (int t = tlo; t <= thi; ++t) {
+            int c = f[t] + k[t];
+            m2 = min(m2, max(m1, c));
+            t1 = (c < m1) ? t : t1;
+            m1 = min(m1, c);
+        }
     }
     const int thr = m1 + thr_add;
     if (m2 > thr) return t1;
@@ -520,8 +533,8 @@ __device__ __forceinline__ void count_edges(const PassParams &p, int edges)
 // optional argmin.  Four rows per thread at a time, their potential-term
 // loads issued together.  Returns how many of the rows' argmins sit on the
 // window's edge.
-template <typename T>
-__device__ __forceinline__ int write_rows_contig(const PassParams &p, const T *lu, const unsigned short *lt,
+template <typename T, typename OFF>
+__device__ __forceinline__ int write_rows_contig(const PassParams &p, const T *lu, const OFF *lt,
                                                   const double *kr64, T *dst, long long xb, int i0, int i1, int step)
 {
     const int N = (int)p.N;
@@ -570,15 +583,17 @@ struct LineInfo {
 };
 
 // One tile of one axis pass (everything a CTA does).  `tmap` is the 3D TMA
-// descriptor of the source for strided lines (unused otherwise).
-template <typename T, int LAYOUT, int ALGO>
+// descriptor of the source for strided lines (unused otherwise).  OFF holds
+// the rows' argmin offsets in shared memory: bytes when the window has at
+// most 256 displacements (more lines per SM), else 16-bit words.
+template <typename T, int LAYOUT, int ALGO, typename OFF = unsigned short>
 __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassParams &p, long long tile)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     T *su = reinterpret_cast<T *>(smem + p.off_u);
     int *fx = reinterpret_cast<int *>(smem + p.off_fx);
     int *kfx = reinterpret_cast<int *>(smem + p.off_kfx);
-    unsigned short *tt = reinterpret_cast<unsigned short *>(smem + p.off_t);
+    OFF *tt = reinterpret_cast<OFF *>(smem + p.off_t);
     double *kr64 = reinterpret_cast<double *>(smem + p.off_k64);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + p.off_misc);
     LineInfo *li = reinterpret_cast<LineInfo *>(smem + p.off_misc + 16);         // [C]
@@ -765,7 +780,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         const bool fallback = li[lsafe].fallback != 0;
         const int *lfx = fx + lsafe * p.lp;
         const int *lk = kfx + lsafe * weff;
-        unsigned short *lt = tt + lsafe * p.tp;
+        OFF *lt = tt + lsafe * p.tp;
         const bool work = active && !fallback;
         int rescans = 0;
         const int S = p.seg, GS = p.gs;
@@ -779,14 +794,14 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 Key2 best = key2_max();
                 int bt = 0;
                 exact_scan<T, LAYOUT>(p, su, kr64, line, r, r, r + weff - 1, best, bt);
-                lt[r] = (unsigned short)bt;
+                lt[r] = (OFF)bt;
             }
             if (g == 0) atomicAdd(&p.counters[CNT_FALLBACK], 1ull);
         }
         if (GS == 1) {
             // P1: every segment's first row scans the whole window
             if (work && s0 < s1)
-                lt[s0] = (unsigned short)screened_row<T, LAYOUT>(p, su, lfx + s0, lk, kr64, line, s0, 0, weff - 1,
+                lt[s0] = (OFF)screened_row<T, LAYOUT>(p, su, lfx + s0, lk, kr64, line, s0, 0, weff - 1,
                                                                 thr_add, rescans);
             __syncthreads();
         } else {
@@ -838,7 +853,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 if (need) tpiv = bt;
                 if (need && o == 0) ++rescans;
             }
-            if (hp && o == 0) lt[rp] = (unsigned short)tpiv;
+            if (hp && o == 0) lt[rp] = (OFF)tpiv;
             __syncthreads();
             // P2: the other segments' first rows, bracketed by the argmins of
             // this group's and the next group's pivot rows (about GS * S
@@ -856,7 +871,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 }
                 const int t = row_or_offload<T, LAYOUT>(p, su, fx, kfx, kr64, lsafe, s0, lo, hi, thr_add, has,
                                                         p.wide_mul * GS * S + p.wide_add, rescans);
-                if (has) lt[s0] = (unsigned short)t;
+                if (has) lt[s0] = (OFF)t;
             }
             __syncthreads();
         }
@@ -886,7 +901,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                     }
                     const int t = row_or_offload<T, LAYOUT>(p, su, fx, kfx, kr64, lsafe, r, tlo, thi, thr_add, has,
                                                             p.wide_mul * (2 * step + 1) + p.wide_add, rescans);
-                    if (has) lt[r] = (unsigned short)t;
+                    if (has) lt[r] = (OFF)t;
                 }
             }
         }
@@ -919,7 +934,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                     xb = rb.base;
                     r1 = min(r1, rb.rows);
                 }
-                edges += write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, xb, r0 + lane, r1, 32);
+                edges += write_rows_contig<T, OFF>(p, su + l * N, tt + l * p.tp, kr64, dst, xb, r0 + lane, r1, 32);
             }
             count_edges(p, edges);
             return;
@@ -928,7 +943,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
         // ---- brute force: every row scanned by a whole warp, shuffle reduction
         const int line = warp / p.wpl;
         if (line < tl.valid) {
-            unsigned short *lt = tt + line * p.tp;
+            OFF *lt = tt + line * p.tp;
             const int wl = warp - line * p.wpl;
             for (int r = wl; r < p.rows; r += p.wpl) {
                 // running minimum as a Key2: the binary64 pipe only does the adds
@@ -951,7 +966,7 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                     const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
                     if (key2_less(ok, best) || (key2_eq(ok, best) && ot < bt)) { best = ok; bt = ot; }
                 }
-                if (lane == 0) lt[r] = (unsigned short)bt;
+                if (lane == 0) lt[r] = (OFF)bt;
             }
         }
     }
@@ -971,13 +986,13 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
                 xb = rb.base;
                 rows = rb.rows;
             }
-            edges = write_rows_contig<T>(p, su + l * N, tt + l * p.tp, kr64, dst, xb, sub, rows, lanes);
+            edges = write_rows_contig<T, OFF>(p, su + l * N, tt + l * p.tp, kr64, dst, xb, sub, rows, lanes);
         }
     } else {
         const int l = tid & (C - 1);
         if (l < tl.valid) {
             const int step = nthr >> p.log2C;
-            const unsigned short *lt = tt + l * p.tp;
+            const OFF *lt = tt + l * p.tp;
             const long long xb = tl.base + l;
             const long long xs = (long long)step * tl.pstride;
             int i = tid >> p.log2C;
@@ -996,12 +1011,12 @@ __device__ __forceinline__ void pass_tile(const CUtensorMap *tmap, const PassPar
     count_edges(p, edges);
 }
 
-template <typename T, int LAYOUT, int ALGO>
+template <typename T, int LAYOUT, int ALGO, typename OFF>
 __global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ CUtensorMap tmap, PassParams p)
 {
     const long long tile = blockIdx.x;
     if (tile >= p.ntiles) return;
-    pass_tile<T, LAYOUT, ALGO>(&tmap, p, tile);
+    pass_tile<T, LAYOUT, ALGO, OFF>(&tmap, p, tile);
 }
 
 // Per-instance fields of a batched pass: one entry per grid of the batch.

@@ -30,6 +30,8 @@ struct AxisPlan {
     long long wait_ns = 500000000LL;       // first TMA wait bound (0.5 s)
     int test_extra_tx = 0;                 // test knob, see apply_test_knobs
     int wide_mul = 2, wide_add = 8;        // warp offload of wide brackets (see PassParams)
+    int t8_ok = 1;                         // MONGE: argmin offsets may be bytes (single-grid launches)
+    int t8 = 0;                            // MONGE: argmin offsets are bytes (weff <= 256 and t8_ok)
     double eta = 0.0;                      // DECOMP: convexity tolerance of the decomposition
     // DECOMP with a period cut across CTAs (dsplit = 1): chunks of dchunk
     // points (dB per line) for the cut, write-back blocks of dvR outputs

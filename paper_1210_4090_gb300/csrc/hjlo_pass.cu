@@ -157,7 +157,7 @@ static void layout_smem(AxisPlan &ax, int esize, int algo)
     ax.off_kfx = (int)off;
     if (monge) off = align_up(off + (size_t)C * ax.weff * 4, 16);
     ax.off_t = (int)off;
-    off = align_up(off + (size_t)C * ax.tp * 2, 16);
+    off = align_up(off + (size_t)C * ax.tp * (ax.t8 ? 1 : 2), 16);
     ax.off_k64 = (int)off;
     off = align_up(off + (size_t)ax.weff * 8, 16);
     ax.off_misc = (int)off;
@@ -334,8 +334,16 @@ static hjlo_status shape_lines(AxisPlan &ax, int esize, int algo, int num_sms, s
     ax.layout = (ax.inner == 1) ? LAYOUT_CONTIG : LAYOUT_STRIDED;
     const long long N = ax.N;
     const long long nlines = ax.inner * ax.outer * std::max(1LL, replicas);
+    // argmin offsets: bytes for the monotone search's single-grid launches
+    // with windows of at most 256 displacements (measured on the 256^3 grid:
+    // 7 CTAs per SM instead of 6, 4.7 % less time per pass), else 16-bit;
+    // the row pitch puts consecutive lines' rows in different banks
+    ax.t8 = (algo == KALGO_MONGE && ax.t8_ok && ax.weff <= 256) ? 1 : 0;
     ax.tp = (int)N;
-    while (ax.tp % 4 != 2) ++ax.tp;
+    if (ax.t8)
+        while (ax.tp % 8 != 4) ++ax.tp;
+    else
+        while (ax.tp % 4 != 2) ++ax.tp;
     if (ax.layout == LAYOUT_STRIDED) {
         ax.nbox = (int)((N + 255) / 256);
         long long per = (N + ax.nbox - 1) / ax.nbox;
